@@ -1,0 +1,316 @@
+"""Pins for the CPU oracle: facts fixed by the paper and by mathematics, not
+by the oracle itself (closed forms, exhaustive search, invariants, reductions,
+hand-derived fixtures in tests/golden/, an independent Python statement).
+
+Section / algorithm numbers refer to Tas, Kaya, Saule, arXiv 1701.02628.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import graphgen as gg
+import oracle as O
+import rs_py
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+POLICIES = [O.FF, O.B1, O.B2, O.B2X]
+NAMES = {O.FF: "FF", O.B1: "B1", O.B2: "B2", O.B2X: "B2X"}
+
+
+def golden(name):
+    with open(os.path.join(GOLDEN, name)) as f:
+        return json.load(f)
+
+
+def nets_of(g):
+    return [g.b_idx[g.b_ptr[v]:g.b_ptr[v + 1]].tolist() for v in range(g.n_b)]
+
+
+def random_tiny(rng, n_a, n_b, pmax):
+    nets = []
+    for _ in range(n_b):
+        s = int(rng.integers(0, min(pmax, n_a) + 1))
+        nets.append(sorted(rng.choice(n_a, size=s, replace=False).tolist()))
+    return gg.from_nets(n_a, nets), nets
+
+
+# --------------------------------------------------------------- closed forms
+
+@pytest.mark.parametrize("n", [3, 4, 7, 12, 64])
+def test_stencil_first_fit_closed_form(n):
+    """9-point stencil Jacobian, natural order: first fit gives
+    c(i, j) = 3 (i mod 3) + (j mod 3) (two columns conflict iff |di|,|dj| <= 2)."""
+    g = gg.stencil9(n)
+    i, j = np.divmod(np.arange(n * n), n)
+    assert np.array_equal(O.seq_color(g), 3 * (i % 3) + (j % 3))
+
+
+def test_single_net_is_a_clique():
+    """One net of size s: every pair conflicts, first fit gives 0..s-1."""
+    for s in [1, 2, 5, 33]:
+        g = gg.from_nets(s, [list(range(s))])
+        assert O.seq_color(g).tolist() == list(range(s))
+        if s <= 20:
+            assert O.bruteforce_min(g) == s
+
+
+def test_disjoint_nets_use_max_net_size_colors():
+    sizes = [3, 7, 1, 5]
+    nets, base = [], 0
+    for s in sizes:
+        nets.append(list(range(base, base + s)))
+        base += s
+    g = gg.from_nets(base, nets)
+    c = O.seq_color(g)
+    assert c.max() + 1 == max(sizes)
+    assert O.conflicts(g, c) == 0
+
+
+def test_no_two_hop_edges_all_zero():
+    """Nets of size <= 1 and isolated vertices: F is always empty."""
+    g = gg.from_nets(6, [[0], [], [3], [5]])
+    assert O.seq_color(g).tolist() == [0] * 6
+    r = O.rs_color(g, chunk=1, waves=1)
+    assert r.rounds == 1 and r.colors.tolist() == [0] * 6
+
+
+def test_d2gc_closed_forms():
+    """D2GC through N[u] nets (Sec. IV): path -> i mod 3; star K_{1,m} ->
+    0..m; cycle C7 -> [0,1,2,0,1,2,3]."""
+    n = 10
+    path = gg.from_edges(n, [(i, i + 1) for i in range(n - 1)])
+    assert O.seq_color(O.closed_nbhd(path)).tolist() == [i % 3 for i in range(n)]
+    m = 6
+    star = gg.from_edges(m + 1, [(0, i) for i in range(1, m + 1)])
+    assert O.seq_color(O.closed_nbhd(star)).tolist() == list(range(m + 1))
+    c7 = gg.from_edges(7, [(i, (i + 1) % 7) for i in range(7)])
+    assert O.seq_color(O.closed_nbhd(c7)).tolist() == [0, 1, 2, 0, 1, 2, 3]
+
+
+def test_closed_nbhd_structure():
+    g = gg.from_edges(5, [(0, 3), (1, 3), (3, 4)])
+    cn = O.closed_nbhd(g)
+    lists = [cn.a_idx[cn.a_ptr[u]:cn.a_ptr[u + 1]].tolist() for u in range(5)]
+    assert lists == [[0, 3], [1, 3], [2], [0, 1, 3, 4], [3, 4]]
+
+
+# ------------------------------------------------------------- brute force
+
+def test_bruteforce_known_values():
+    """Chromatic numbers of small conflict graphs: nets = edges of C5 -> 3,
+    C6 -> 2, K4 -> 4, no nets -> 1."""
+    c5 = gg.from_nets(5, [[i, (i + 1) % 5] for i in range(5)])
+    c6 = gg.from_nets(6, [[i, (i + 1) % 6] for i in range(6)])
+    k4 = gg.from_nets(4, [[0, 1, 2, 3]])
+    empty = gg.from_nets(3, [])
+    assert [O.bruteforce_min(g) for g in (c5, c6, k4, empty)] == [3, 2, 4, 1]
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_greedy_never_beats_optimum_and_is_valid(seed):
+    rng = np.random.default_rng(seed)
+    g, _ = random_tiny(rng, int(rng.integers(2, 10)), int(rng.integers(1, 8)), 4)
+    opt = O.bruteforce_min(g)
+    for pol in POLICIES:
+        c = O.seq_color(g, pol)
+        assert O.conflicts(g, c) == 0
+        assert c.max() + 1 >= opt
+        r = O.rs_color(g, pol, chunk=2, waves=2, big_net=2)
+        assert r.status == O.OK and O.conflicts(g, r.colors) == 0
+        assert r.colors.max() + 1 >= opt
+
+
+def test_d2gc_valid_by_direct_distance_definition():
+    """Colorings from N[u] nets are valid for the shortest-path definition
+    of D2GC (Sec. II), checked by a direct depth-2 walk."""
+    ug = gg.rmat(9, 8, seed=5)
+    cn = O.closed_nbhd(ug)
+    for pol in POLICIES:
+        assert O.d2_conflicts(ug, O.seq_color(cn, pol)) == 0
+        r = O.rs_color(cn, pol, chunk=8, waves=4, big_net=16)
+        assert r.status == O.OK and O.d2_conflicts(ug, r.colors) == 0
+    bad = O.seq_color(cn).copy()
+    nb = ug.idx[ug.ptr[0]:ug.ptr[1]]
+    if len(nb) >= 2:  # two neighbours of vertex 0 are at distance 2
+        bad[nb[1]] = bad[nb[0]]
+        assert O.d2_conflicts(ug, bad) > 0
+
+
+# ---------------------------------------------------------- greedy bound
+
+@pytest.mark.parametrize("pol", POLICIES)
+def test_greedy_bound(pol):
+    """#colors <= max_w |nbor(w)| + 1 for every policy; first fit also has
+    c[w] <= |nbor(w)| per vertex (Alg. 2 picks the smallest of |F|+1 colors)."""
+    g = gg.random_bipartite(500, 300, 4, seed=7)
+    best, sizes = O.max_nbor(g)
+    c = O.seq_color(g, pol)
+    assert c.max() <= best
+    r = O.rs_color(g, pol, chunk=16, waves=4, big_net=8)
+    assert r.colors.max() <= best
+    if pol == O.FF:
+        assert np.all(c <= sizes) and np.all(r.colors <= sizes)
+
+
+# ------------------------------------------------------ RS reductions
+
+@pytest.mark.parametrize("pol", POLICIES)
+def test_rs_with_one_chunk_is_sequential(pol):
+    """RS(C >= |V_A|, any Q, T = inf) is the sequential greedy, bit-exact."""
+    g = gg.random_bipartite(300, 200, 5, seed=3)
+    rank = np.random.default_rng(1).permutation(g.n_a).astype(np.int32)
+    for Q in (1, 3, 16):
+        r = O.rs_color(g, pol, chunk=g.n_a, waves=Q, big_net=O.NO_BIG)
+        assert r.rounds == 1
+        assert np.array_equal(r.colors, O.seq_color(g, pol))
+        r = O.rs_color(g, pol, chunk=g.n_a + 5, waves=Q, big_net=O.NO_BIG, rank=rank)
+        assert np.array_equal(r.colors, O.seq_color(g, pol, rank=rank))
+
+
+def test_rs_jacobi_on_a_clique_takes_s_rounds():
+    """RS(1, 1, inf) is the literal Jacobi reading: on one net of size s all
+    members pick the same first-fit color each round and only the lowest rank
+    keeps it, so there are s rounds and c[u_i] = i."""
+    s = 9
+    g = gg.from_nets(s, [list(range(s))])
+    r = O.rs_color(g, O.FF, chunk=1, waves=1, big_net=O.NO_BIG)
+    assert r.rounds == s and r.colors.tolist() == list(range(s))
+    assert r.w_per_round.tolist() == list(range(s, 0, -1))
+
+
+def test_rs_round_count_bound_and_first_vertex_survives():
+    g = gg.random_bipartite(400, 50, 6, seed=11)
+    r = O.rs_color(g, O.FF, chunk=1, waves=1, big_net=O.NO_BIG)
+    assert r.status == O.OK and r.rounds <= g.n_a
+    assert np.all(np.diff(r.w_per_round) < 0)  # the lowest-rank W vertex always keeps its color
+
+
+def test_rs_round_cap():
+    g = gg.from_nets(6, [list(range(6))])
+    r = O.rs_color(g, O.FF, chunk=1, waves=1, big_net=O.NO_BIG, max_rounds=3)
+    assert r.status == O.EROUNDS
+
+
+def test_rs_thread_count_invariance():
+    g = gg.chung_lu(20000, 16, 1500, 2.1, seed=4)
+    base = O.rs_color(g, O.B2, chunk=64, waves=16, big_net=64, nthreads=1)
+    for t in (2, 3, 8):
+        r = O.rs_color(g, O.B2, chunk=64, waves=16, big_net=64, nthreads=t)
+        assert np.array_equal(r.colors, base.colors)
+        assert np.array_equal(r.w_per_round, base.w_per_round)
+
+
+def test_traversal_of_round_one_is_e2():
+    """Round 1 traverses sum_v |vtxs(v)| (|vtxs(v)| - 1) two-hop entries,
+    the cost of one vertex-based sweep (Sec. III)."""
+    g = gg.random_bipartite(2000, 2000, 5, seed=1)
+    s = np.diff(g.b_ptr).astype(np.int64)
+    r = O.rs_color(g)
+    assert r.trav_per_round[0] == int((s * (s - 1)).sum())
+    assert r.w_per_round[0] == g.n_a
+
+
+# ---------------------------------------------------------- golden fixtures
+
+@pytest.mark.parametrize("name", ["rs_overlay_waves.json", "rs_reverse_first_fit.json",
+                                  "rs_reverse_fallback.json"])
+def test_golden_rs(name):
+    fx = golden(name)
+    g = gg.from_nets(fx["n_a"], fx["nets"])
+    p = fx["params"]
+    r = O.rs_color(g, p["policy"], chunk=p["chunk"], waves=p["waves"], big_net=p["big_net"])
+    e = fx["expected"]
+    assert r.status == O.OK
+    assert r.colors.tolist() == e["colors"]
+    assert r.rounds == e["rounds"]
+    assert r.w_per_round.tolist() == e["w_per_round"]
+    assert r.trav_per_round.tolist() == e["trav_per_round"]
+    c_py, hist = rs_py.rs(fx["n_a"], fx["nets"], p["policy"], p["chunk"], p["waves"], p["big_net"])
+    assert c_py == e["colors"] and hist == e["w_per_round"]
+
+
+def test_golden_sequential_balancing():
+    fx = golden("seq_balancing.json")
+    g = gg.from_nets(fx["n_a"], fx["nets"])
+    for pol in POLICIES:
+        assert O.seq_color(g, pol).tolist() == fx["expected"][NAMES[pol]]
+        assert rs_py.seq(fx["n_a"], fx["nets"], pol) == fx["expected"][NAMES[pol]]
+
+
+def test_golden_chunk_state():
+    fx = golden("rs_chunk_state.json")
+    g = gg.from_nets(fx["n_a"], fx["nets"])
+    for pname, pol in (("B1", O.B1), ("B2", O.B2), ("FF", O.FF)):
+        out = O.rs_chunks(g, fx["S"], fx["W"], fx["chunks"], pol,
+                          chunk=fx["params"]["chunk"], big_net=fx["params"]["big_net"])
+        assert out.tolist() == fx["expected"][pname]
+
+
+def test_balance_statistics():
+    c = np.array([0, 1, 2, 0, 2, 0], np.int32)
+    K, card = O.color_sets(c)
+    assert K == 3 and card.tolist() == [3, 1, 2]
+    b = O.balance(c)
+    assert b["max_card"] == 3 and b["mean_card"] == 2.0
+    assert abs(b["std_card"] - np.std([3, 1, 2])) < 1e-12
+    K, card = O.color_sets(np.array([4, 4, 0], np.int32))
+    assert K == 2 and card.tolist() == [1, 0, 0, 0, 2]
+
+
+# ------------------------------------- independent Python statement of RS
+
+@pytest.mark.parametrize("seed", range(40))
+def test_rs_matches_independent_python(seed):
+    rng = np.random.default_rng(100 + seed)
+    n_a = int(rng.integers(1, 40))
+    g, nets = random_tiny(rng, n_a, int(rng.integers(0, 25)), 12)
+    pol = int(rng.integers(0, 4))
+    C = int(rng.integers(1, 9))
+    Q = int(rng.integers(1, 5))
+    T = int(rng.choice([1, 2, 4, 8, O.NO_BIG]))
+    rank = rng.permutation(n_a).astype(np.int32) if seed % 3 == 0 else None
+    r = O.rs_color(g, pol, chunk=C, waves=Q, big_net=T, rank=rank)
+    c_py, hist = rs_py.rs(n_a, nets, pol, C, Q, T, None if rank is None else rank.tolist())
+    assert r.status == O.OK
+    assert r.colors.tolist() == c_py
+    assert r.w_per_round.tolist() == hist
+    assert O.seq_color(g, pol, rank=rank).tolist() == rs_py.seq(
+        n_a, nets, pol, None if rank is None else rank.tolist())
+
+
+# -------------------------------- wave stepping (used by full-size parity)
+
+def test_wave_stepping_reproduces_full_run():
+    """Stopping after each wave and recoloring that wave's chunks with
+    rs_chunks, then applying the conflict rule, reproduces the full run."""
+    g = gg.random_bipartite(700, 500, 5, seed=9)
+    C, Q, T, pol = 16, 4, 6, O.B1
+    full = O.rs_color(g, pol, chunk=C, waves=Q, big_net=T)
+    total_waves = full.rounds * Q
+    for wv in range(1, total_waves):
+        st = O.rs_color(g, pol, chunk=C, waves=Q, big_net=T, stop_after_waves=wv)
+        assert st.status == O.STOPPED
+        nxt = O.rs_color(g, pol, chunk=C, waves=Q, big_net=T, stop_after_waves=wv + 1)
+        nch = (st.m + C - 1) // C
+        q = st.wave
+        chunks = list(range(q * nch // Q, (q + 1) * nch // Q))
+        out = O.rs_chunks(g, st.colors, st.W, chunks, pol, chunk=C, big_net=T)
+        pos = [p for j in chunks for p in range(j * C, min(st.m, (j + 1) * C))]
+        if nxt.status == O.STOPPED and nxt.wave == q + 1:
+            assert np.array_equal(out[pos], nxt.colors[st.W[pos]])
+    # conflict rule on the last round's colors
+    st = O.rs_color(g, pol, chunk=C, waves=Q, big_net=T, stop_after_waves=Q - 1)
+    nch = (st.m + C - 1) // C
+    chunks = list(range((Q - 1) * nch // Q, nch))
+    out = O.rs_chunks(g, st.colors, st.W, chunks, pol, chunk=C, big_net=T)
+    c = st.colors.copy()
+    for j in chunks:
+        for p in range(j * C, min(st.m, (j + 1) * C)):
+            c[st.W[p]] = out[p]
+    lose, rc = O.rs_losers(g, c, st.W, np.arange(st.m))
+    assert rc == O.OK
+    r2 = O.rs_color(g, pol, chunk=C, waves=Q, big_net=T, stop_after_waves=Q)
+    if r2.status == O.STOPPED:
+        assert np.array_equal(r2.W, st.W[lose.astype(bool)])
