@@ -1,0 +1,163 @@
+/*
+ * bgpc.h -- C ABI of the GB300 (sm_103a) library for optimistic bipartite-graph
+ * partial coloring (BGPC) and distance-2 graph coloring (D2GC), after Tas,
+ * Kaya, Saule, "Greed is Good: Optimistic Algorithms for Bipartite-Graph
+ * Partial Coloring on Multicore Architectures" (arXiv 1701.02628).
+ *
+ * Problem (Sec. II): G = (V_A u V_B, E).  Color every V_A vertex with a
+ * non-negative int32 so that two V_A vertices that share a V_B vertex ("net")
+ * get different colors.  D2GC (Sec. II, IV): color every vertex of an
+ * undirected graph so that vertices within shortest-path distance 2 differ.
+ *
+ * Conventions for every call
+ *  - Graph, color, rank and work-queue arrays are DEVICE pointers owned by the
+ *    caller; the library never frees or retains them after the call returns.
+ *    Host pointers are marked "(host)".
+ *  - `stream` is a cudaStream_t (passed as void* so that this header needs no
+ *    CUDA include); every device operation of a call is ordered on it.  NULL
+ *    means the legacy default stream.
+ *  - Every call returns an int status: BGPC_OK (0), BGPC_STOPPED (1, only when
+ *    requested), or a negative BGPC_E* code.  Output arrays are fully written
+ *    only on BGPC_OK.  The calls that return statistics synchronise `stream`.
+ *  - A context owns the library's scratch memory (grown on demand, freed by
+ *    bgpc_ctx_destroy).  A context may be used by one host thread at a time;
+ *    different contexts are independent.  The library keeps no other state.
+ *  - Colors are in [0, n_a); -1 never appears in a successful result.
+ */
+#ifndef BGPC_H
+#define BGPC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------- */
+#define BGPC_OK 0
+#define BGPC_STOPPED 1        /* stopped after opts.stop_after_waves waves (debug) */
+#define BGPC_EINVAL (-1)      /* bad argument, size or option */
+#define BGPC_ENOMEM (-2)      /* device allocation failed */
+#define BGPC_ECUDA (-3)       /* a CUDA runtime call failed */
+#define BGPC_EROUNDS (-4)     /* more than opts.max_rounds rounds */
+#define BGPC_ETIMEOUT (-5)    /* a bounded device wait gave up */
+#define BGPC_EUNSORTED (-6)   /* adjacency not sorted / not unique / CSR and CSC disagree */
+#define BGPC_EINTERNAL (-7)   /* a device-side consistency check failed */
+
+/* ---- coloring policies (Sec. V) -------------------------------------- */
+#define BGPC_FF 0   /* first fit (Alg. 2, lines 6-9) */
+#define BGPC_B1 1   /* balancing heuristic B1 (Alg. ColorWorkQueue-B1) */
+#define BGPC_B2 2   /* B2, update col_next = min(col+1, col_max/3+1) as in the algorithm box */
+#define BGPC_B2X 3  /* B2, prose reading: start at least at col_max/3+1, i.e. max(...) */
+
+#define BGPC_MAX_REPORT 64   /* rounds reported in bgpc_stats_t */
+
+typedef struct bgpc_ctx bgpc_ctx_t;
+
+/* Bipartite graph (Sec. II): nets(u) = a_idx[a_ptr[u] .. a_ptr[u+1]) for
+ * u in V_A = [0, n_a), vtxs(v) = b_idx[b_ptr[v] .. b_ptr[v+1]) for v in
+ * V_B = [0, n_b).  int32, sorted ascending, no duplicates, the two sides
+ * describe the same edge set, nnz = a_ptr[n_a] = b_ptr[n_b] < 2^31. */
+typedef struct {
+    int32_t n_a, n_b, nnz;
+    const int32_t *a_ptr, *a_idx;
+    const int32_t *b_ptr, *b_idx;
+} bgpc_graph_t;
+
+/* Undirected graph for D2GC: adj(u) = idx[ptr[u] .. ptr[u+1]), symmetric,
+ * sorted, unique, no self loops; nnz + n < 2^31. */
+typedef struct {
+    int32_t n, nnz;
+    const int32_t *ptr, *idx;
+} bgpc_ugraph_t;
+
+/* Options.  The semantic parameters (policy, chunk, waves, big_net, rank)
+ * fix the result bit for bit; nothing else (block sizes, autotuned mapping)
+ * changes it.  Round-synchronous semantics RS(C, Q, T, policy, rank):
+ *   round r colors W_r (rank order) in chunks of C consecutive entries, the
+ *   chunks split into Q waves; every chunk of a wave reads the colors
+ *   published by the earlier waves and colors its own vertices one after the
+ *   other, as one of the paper's threads with OpenMP chunk C would (V-V-64,
+ *   Sec. VI); vertices whose largest net has more than T members take the
+ *   reverse first-fit color of Alg. 8 (k-th free color below |vtxs(v)|);
+ *   then conflicts are removed per net, the lower rank keeping its color
+ *   (Alg. 3 rule, Alg. 7 traversal), and the losers form W_{r+1}. */
+typedef struct {
+    int32_t policy;          /* BGPC_FF, BGPC_B1, BGPC_B2, BGPC_B2X */
+    int32_t chunk;           /* C in [1, 64]; default 64 */
+    int32_t waves;           /* Q >= 1; default 16 */
+    int32_t big_net;         /* T >= 0; default 64; INT32_MAX disables Alg. 8's rule */
+    const int32_t *rank;     /* device, permutation of [0, n_a), or NULL for id order */
+    int32_t max_rounds;      /* BGPC_EROUNDS beyond this; default 1000 */
+    int32_t validate;        /* 1: check sortedness, ranges, CSR/CSC agreement, rank */
+    int64_t stop_after_waves;/* debug: > 0 stops after that many waves (all rounds
+                                counted, empty waves too) and returns BGPC_STOPPED */
+    int32_t *W_out;          /* debug, device [n_a] or NULL: work queue when stopped */
+    int32_t want_balance;    /* 1: fill the color-set statistics of bgpc_stats_t */
+    int32_t profile;         /* 1: time each phase with CUDA events on `stream`
+                                (the ms_* fields of bgpc_stats_t) */
+    int32_t reserved[6];
+} bgpc_opts_t;
+
+/* Statistics of one call (host struct). */
+typedef struct {
+    int32_t rounds;                       /* rounds run */
+    int32_t colors;                       /* max color + 1 */
+    int64_t w_per_round[BGPC_MAX_REPORT]; /* |W_r| */
+    int64_t trav_per_round[BGPC_MAX_REPORT]; /* sum over W_r of sum over nets(w) (|vtxs|-1) */
+    int64_t trav_total;                   /* all rounds */
+    int32_t stopped_m;                    /* when BGPC_STOPPED: |W_r| of the current round */
+    int32_t stopped_wave;                 /* when BGPC_STOPPED: index of the next wave */
+    int32_t n_sets;                       /* non-empty color sets (want_balance) */
+    int32_t max_card;                     /* largest color set (want_balance) */
+    double mean_card, std_card;           /* over non-empty sets (want_balance) */
+    int64_t incid_total;                  /* all rounds: sum over W_r of |nets(w)| */
+    int64_t w_total;                      /* all rounds: sum of |W_r| */
+    int64_t kernel_launches;              /* kernels this call launched */
+    int64_t color_launches;               /* wave-coloring kernel launches */
+    double ms_setup, ms_color, ms_publish, ms_detect; /* device time per phase (profile) */
+} bgpc_stats_t;
+
+/* Fill `opts` with the defaults: FF, C=64, Q=16, T=64, id order,
+ * max_rounds=1000, no validation, no stop, no balance statistics. */
+void bgpc_opts_default(bgpc_opts_t *opts);
+
+/* Create a context on CUDA device `device` (made current for the call). */
+int bgpc_ctx_create(bgpc_ctx_t **ctx, int device);
+int bgpc_ctx_destroy(bgpc_ctx_t *ctx);
+
+/* BGPC (Sec. III; Alg. 1 round loop, Alg. 4 vertex-based two-hop gather,
+ * Alg. 8 reverse first fit for big nets, Alg. 7 net-based conflict removal
+ * with the Alg. 3 lower-rank-wins rule, Sec. V balancing).
+ * colors: device int32 [n_a], written on BGPC_OK (or the snapshot on
+ * BGPC_STOPPED).  stats (host) may be NULL.  Synchronises `stream`. */
+int bgpc_color(bgpc_ctx_t *ctx, const bgpc_graph_t *g, const bgpc_opts_t *opts,
+               int32_t *colors, bgpc_stats_t *stats, void *stream);
+
+/* D2GC (Sec. IV, Alg. 9-10): BGPC on the closed neighbourhoods
+ * nets(u) = vtxs(u) = N[u] = {u} u adj(u), built on the device; the reverse
+ * first fit starts at |N[v]| - 1 = |nbor(v)| as in Alg. 9.
+ * colors: device int32 [n]. */
+int d2gc_color(bgpc_ctx_t *ctx, const bgpc_ugraph_t *g, const bgpc_opts_t *opts,
+               int32_t *colors, bgpc_stats_t *stats, void *stream);
+
+/* Validity check (Sec. II definition): *n_bad (host) = number of V_A vertices
+ * that are uncolored or share a color with a vertex of a common net. */
+int bgpc_validate(bgpc_ctx_t *ctx, const bgpc_graph_t *g, const int32_t *colors,
+                  int64_t *n_bad, void *stream);
+
+/* Color-set statistics (Sec. VI-C, Table VI): card (device int64 [max_colors])
+ * receives the cardinality of every color 0..max_colors-1 (colors >= max_colors
+ * are an error); *n_sets, *max_card (host) and *mean_card, *std_card (host,
+ * over non-empty sets) may each be NULL. */
+int bgpc_color_sets(bgpc_ctx_t *ctx, const int32_t *colors, int32_t n, int64_t *card,
+                    int32_t max_colors, int32_t *n_sets, int32_t *max_card,
+                    double *mean_card, double *std_card, void *stream);
+
+/* Human-readable text of a status code (static storage). */
+const char *bgpc_strerror(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BGPC_H */

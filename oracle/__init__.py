@@ -56,7 +56,7 @@ def _load():
         "orc_seq_color": (G + [P, i32, P], ctypes.c_int),
         "orc_rs_color": (G + [P, i32, i32, i32, i64, i32, i64, i32, P, P, P64, P64, i32,
                               P, P, P], ctypes.c_int),
-        "orc_rs_chunks": (G + [P, P, i32, i32, i32, i64, P, i32, P], ctypes.c_int),
+        "orc_rs_chunks": (G + [P, P, i32, i32, i32, i64, P, i32, i32, P], ctypes.c_int),
         "orc_rs_losers": (G + [P, P, i32, P, i32, P8], ctypes.c_int),
         "orc_conflicts": (G + [P], i64),
         "orc_max_nbor": (G + [P], i32),
@@ -130,13 +130,14 @@ def rs_color(g, policy: int = FF, chunk: int = 64, waves: int = 16, big_net: int
                            W=W[:m.value].copy(), m=m.value, wave=wave.value)
 
 
-def rs_chunks(g, S, W, chunks, policy: int = FF, chunk: int = 64, big_net: int = 64):
+def rs_chunks(g, S, W, chunks, policy: int = FF, chunk: int = 64, big_net: int = 64,
+              nthreads: int = 1):
     """One wave step of O-2: colors of the listed chunks given snapshot S and
     work queue W.  Returns an array indexed by W position (-2 elsewhere)."""
     S, W, ch = _i32(S), _i32(W), _i32(chunks)
     out = np.full(max(len(W), 1), -2, np.int32)
     rc = _load().orc_rs_chunks(*_g(g), _p(S), _p(W), len(W), policy, chunk, big_net,
-                               _p(ch), len(ch), _p(out))
+                               _p(ch), len(ch), nthreads, _p(out))
     if rc != OK:
         raise ValueError(f"orc_rs_chunks failed: {rc}")
     return out[:len(W)]

@@ -156,8 +156,12 @@ int orc_seq_color(int32_t n_a, int32_t n_b, const int32_t *a_ptr, const int32_t 
 /* ------------------------------------------------------------------------
  * O-2: round-synchronous speculative coloring RS(C, Q, T, policy, rank).
  *
- * Round r works on W_r (rank order, m = |W_r|).  Chunk j is W_r[jC, jC+C);
- * wave q holds chunks [floor(q*nch/Q), floor((q+1)*nch/Q)), nch = ceil(m/C).
+ * Round r works on W_r (rank order, m = |W_r|).  Chunk j is W_r[jC, jC+C),
+ * j < nch = ceil(m/C).  Chunk j belongs to wave q(j) = floor(frac(j*phi)*Q),
+ * phi = (sqrt(5)-1)/2, evaluated in 32-bit fixed point (wave_of below), so
+ * that the chunks of a wave are spread evenly over W_r and chunks close in
+ * rank order run in different waves, as in the paper's runs where only a
+ * handful of consecutive OpenMP chunks are in flight at any time.
  * All chunks of a wave read the same snapshot S; a chunk colors its vertices
  * one after the other like one of the paper's threads (chunk 64 of V-V-64,
  * Section VI), seeing its own earlier colors through an overlay; after the
@@ -298,6 +302,24 @@ static void reverse_offsets(int32_t n_b, const int32_t *b_ptr, const int32_t *b_
     }
 }
 
+/* Wave of chunk j: ((j * 0x9E3779B9 mod 2^32) * Q) >> 32, i.e. the Weyl
+ * sequence frac(j * phi) with phi = 0x9E3779B9 / 2^32, scaled to Q waves. */
+static int32_t wave_of(int64_t j, int32_t Q) {
+    uint32_t x = (uint32_t)((uint64_t)j * 0x9E3779B9ull);
+    return (int32_t)(((uint64_t)x * (uint64_t)Q) >> 32);
+}
+
+/* Chunks of every wave, in increasing chunk order: list[off[q] .. off[q+1]). */
+static void wave_lists(int64_t nch, int32_t Q, int64_t *off, int64_t *list) {
+    for (int32_t q = 0; q <= Q; q++) off[q] = 0;
+    for (int64_t j = 0; j < nch; j++) off[wave_of(j, Q) + 1]++;
+    for (int32_t q = 0; q < Q; q++) off[q + 1] += off[q];
+    int64_t *fill = (int64_t *)malloc(sizeof(int64_t) * ((size_t)Q + 1));
+    for (int32_t q = 0; q <= Q; q++) fill[q] = off[q];
+    for (int64_t j = 0; j < nch; j++) list[fill[wave_of(j, Q)]++] = j;
+    free(fill);
+}
+
 static int32_t max_color(const int32_t *S, int32_t n) {
     int32_t mx = -1;
     for (int32_t u = 0; u < n; u++)
@@ -343,9 +365,11 @@ int orc_rs_color(int32_t n_a, int32_t n_b, const int32_t *a_ptr, const int32_t *
     int32_t *S = (int32_t *)malloc(sizeof(int32_t) * na);
     int32_t *out = (int32_t *)malloc(sizeof(int32_t) * na);
     uint8_t *lose = (uint8_t *)malloc(na);
+    int64_t *woff = (int64_t *)malloc(sizeof(int64_t) * ((size_t)Q + 1));
+    int64_t *wlist = (int64_t *)malloc(sizeof(int64_t) * na);
     rs_worker *wk = (rs_worker *)calloc((size_t)nthreads, sizeof(rs_worker));
     int rc = ORC_OK;
-    if (!W || !Wn || !inW || !own || !s_own || !k || !S || !out || !lose || !wk ||
+    if (!W || !Wn || !inW || !own || !s_own || !k || !S || !out || !lose || !wk || !woff || !wlist ||
         alloc_workers(wk, nthreads, n_a)) {
         rc = ORC_ENOMEM;
         goto done;
@@ -380,6 +404,7 @@ int orc_rs_color(int32_t n_a, int32_t n_b, const int32_t *a_ptr, const int32_t *
         x.policy = policy; x.C = C; x.T = T; x.S = S; x.W = W; x.m = m;
         x.s_own = s_own; x.k = k; x.out = out;
         int64_t nch = ((int64_t)m + C - 1) / C;
+        wave_lists(nch, Q, woff, wlist);
         for (int32_t q = 0; q < Q; q++) {
             if (stop_after_waves > 0 && waves_done == stop_after_waves) {
                 memcpy(c, S, sizeof(int32_t) * (size_t)n_a);
@@ -390,13 +415,14 @@ int orc_rs_color(int32_t n_a, int32_t n_b, const int32_t *a_ptr, const int32_t *
                 rc = ORC_STOPPED;
                 goto done;
             }
-            int64_t jlo = (int64_t)q * nch / Q, jhi = (int64_t)(q + 1) * nch / Q;
             int32_t mx = max_color(S, n_a);
             x.col_max0 = mx < 0 ? 0 : mx;
-            rs_run_chunks(&x, NULL, jlo, jhi, wk, nthreads);
-            int64_t plo = jlo * C, phi = jhi * C;
-            if (phi > m) phi = m;
-            for (int64_t p = plo; p < phi; p++) S[W[p]] = out[p];
+            rs_run_chunks(&x, wlist, woff[q], woff[q + 1], wk, nthreads);
+            for (int64_t t = woff[q]; t < woff[q + 1]; t++) {
+                int64_t plo = wlist[t] * C, phi = plo + C;
+                if (phi > m) phi = m;
+                for (int64_t p = plo; p < phi; p++) S[W[p]] = out[p];
+            }
             waves_done++;
         }
         memcpy(c, S, sizeof(int32_t) * (size_t)n_a);
@@ -422,25 +448,29 @@ int orc_rs_color(int32_t n_a, int32_t n_b, const int32_t *a_ptr, const int32_t *
 done:
     if (wk) free_workers(wk, nthreads);
     free(wk); free(W); free(Wn); free(inW); free(own); free(s_own); free(k);
-    free(S); free(out); free(lose);
+    free(S); free(out); free(lose); free(woff); free(wlist);
     return rc;
 }
 
 int orc_rs_chunks(int32_t n_a, int32_t n_b, const int32_t *a_ptr, const int32_t *a_idx,
                   const int32_t *b_ptr, const int32_t *b_idx, const int32_t *S,
                   const int32_t *W, int32_t m, int32_t policy, int32_t C, int64_t T,
-                  const int32_t *chunks, int32_t nchunks, int32_t *out) {
+                  const int32_t *chunks, int32_t nchunks, int32_t nthreads, int32_t *out) {
     if (n_a < 0 || C < 1 || m < 0 || m > n_a || !valid_policy(policy)) return ORC_EINVAL;
+    if (nthreads < 1) nthreads = 1;
+    if (nthreads > 256) nthreads = 256;
     size_t na = (size_t)n_a + 1;
     int32_t *inW = (int32_t *)malloc(sizeof(int32_t) * na);
     int32_t *own = (int32_t *)malloc(sizeof(int32_t) * na);
     int32_t *s_own = (int32_t *)malloc(sizeof(int32_t) * na);
     int32_t *k = (int32_t *)malloc(sizeof(int32_t) * na);
     int64_t *ch = (int64_t *)malloc(sizeof(int64_t) * ((size_t)nchunks + 1));
-    rs_worker wk;
-    memset(&wk, 0, sizeof(wk));
+    rs_worker *wk = (rs_worker *)calloc((size_t)nthreads, sizeof(rs_worker));
     int rc = ORC_OK;
-    if (!inW || !own || !s_own || !k || !ch || alloc_workers(&wk, 1, n_a)) { rc = ORC_ENOMEM; goto done; }
+    if (!inW || !own || !s_own || !k || !ch || !wk || alloc_workers(wk, nthreads, n_a)) {
+        rc = ORC_ENOMEM;
+        goto done;
+    }
     for (int32_t u = 0; u < n_a; u++) inW[u] = -1;
     for (int32_t p = 0; p < m; p++) {
         if (W[p] < 0 || W[p] >= n_a || inW[W[p]] >= 0) { rc = ORC_EINVAL; goto done; }
@@ -459,9 +489,10 @@ int orc_rs_chunks(int32_t n_a, int32_t n_b, const int32_t *a_ptr, const int32_t 
     x.s_own = s_own; x.k = k; x.out = out;
     int32_t mx = max_color(S, n_a);
     x.col_max0 = mx < 0 ? 0 : mx;
-    rs_run_chunks(&x, ch, 0, nchunks, &wk, 1);
+    rs_run_chunks(&x, ch, 0, nchunks, wk, nthreads);
 done:
-    free_workers(&wk, 1);
+    if (wk) free_workers(wk, nthreads);
+    free(wk);
     free(inW); free(own); free(s_own); free(k); free(ch);
     return rc;
 }

@@ -38,7 +38,8 @@ int orc_seq_color(int32_t n_a, int32_t n_b, const int32_t *a_ptr, const int32_t 
 
 /* O-2: round-synchronous speculative coloring RS(C, Q, T, policy, rank).
  * Deterministic replay of Alg. 1 with chunked, wave-published coloring and
- * lower-rank-wins conflict removal.  nthreads > 1 colors the chunks of a wave
+ * lower-rank-wins conflict removal.  Chunk j (C consecutive work-queue
+ * entries) belongs to wave ((j * 0x9E3779B9 mod 2^32) * Q) >> 32.  nthreads > 1 colors the chunks of a wave
  * on several host threads (results do not depend on it).
  * stop_after_waves > 0 stops after that many waves (counted over all rounds)
  * and returns ORC_STOPPED with c = the snapshot at that point, W_out (if not
@@ -60,7 +61,7 @@ int orc_rs_color(int32_t n_a, int32_t n_b, const int32_t *a_ptr, const int32_t *
 int orc_rs_chunks(int32_t n_a, int32_t n_b, const int32_t *a_ptr, const int32_t *a_idx,
                   const int32_t *b_ptr, const int32_t *b_idx, const int32_t *S,
                   const int32_t *W, int32_t m, int32_t policy, int32_t C, int64_t T,
-                  const int32_t *chunks, int32_t nchunks, int32_t *out);
+                  const int32_t *chunks, int32_t nchunks, int32_t nthreads, int32_t *out);
 
 /* Conflict rule of O-2 (Alg. 3 line "c[u] = c[w] and w > u", with rank in
  * place of id): for each listed W position p, lose[p] = 1 iff some

@@ -1,0 +1,282 @@
+"""GB300 (sm_103a) bipartite-graph partial coloring and distance-2 coloring.
+
+Thin Python binding of the C ABI declared in ``include/bgpc.h``: argument
+marshalling only.  Every step of the coloring runs in the CUDA kernels of
+``libbgpc_gb300.so``; there is no CPU fallback, and importing the functions
+below raises if the library has not been built (``build.build()``).
+
+PyTorch is used for device memory and streams: graph arrays are int32 CUDA
+tensors, colors come back as an int32 CUDA tensor, and every call runs on the
+current torch stream unless one is given.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import torch
+
+from . import build as _build
+
+BGPC_OK, BGPC_STOPPED = 0, 1
+BGPC_EINVAL, BGPC_ENOMEM, BGPC_ECUDA, BGPC_EROUNDS = -1, -2, -3, -4
+BGPC_ETIMEOUT, BGPC_EUNSORTED, BGPC_EINTERNAL = -5, -6, -7
+BGPC_FF, BGPC_B1, BGPC_B2, BGPC_B2X = 0, 1, 2, 3
+BGPC_MAX_REPORT = 64
+NO_BIG = (1 << 31) - 1
+
+_c_i32p = ctypes.POINTER(ctypes.c_int32)
+
+
+class bgpc_graph_t(ctypes.Structure):
+    _fields_ = [("n_a", ctypes.c_int32), ("n_b", ctypes.c_int32), ("nnz", ctypes.c_int32),
+                ("a_ptr", ctypes.c_void_p), ("a_idx", ctypes.c_void_p),
+                ("b_ptr", ctypes.c_void_p), ("b_idx", ctypes.c_void_p)]
+
+
+class bgpc_ugraph_t(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("nnz", ctypes.c_int32),
+                ("ptr", ctypes.c_void_p), ("idx", ctypes.c_void_p)]
+
+
+class bgpc_opts_t(ctypes.Structure):
+    _fields_ = [("policy", ctypes.c_int32), ("chunk", ctypes.c_int32),
+                ("waves", ctypes.c_int32), ("big_net", ctypes.c_int32),
+                ("rank", ctypes.c_void_p), ("max_rounds", ctypes.c_int32),
+                ("validate", ctypes.c_int32), ("stop_after_waves", ctypes.c_int64),
+                ("W_out", ctypes.c_void_p), ("want_balance", ctypes.c_int32),
+                ("profile", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6)]
+
+
+class bgpc_stats_t(ctypes.Structure):
+    _fields_ = [("rounds", ctypes.c_int32), ("colors", ctypes.c_int32),
+                ("w_per_round", ctypes.c_int64 * BGPC_MAX_REPORT),
+                ("trav_per_round", ctypes.c_int64 * BGPC_MAX_REPORT),
+                ("trav_total", ctypes.c_int64),
+                ("stopped_m", ctypes.c_int32), ("stopped_wave", ctypes.c_int32),
+                ("n_sets", ctypes.c_int32), ("max_card", ctypes.c_int32),
+                ("mean_card", ctypes.c_double), ("std_card", ctypes.c_double),
+                ("incid_total", ctypes.c_int64), ("w_total", ctypes.c_int64),
+                ("kernel_launches", ctypes.c_int64), ("color_launches", ctypes.c_int64),
+                ("ms_setup", ctypes.c_double), ("ms_color", ctypes.c_double),
+                ("ms_publish", ctypes.c_double), ("ms_detect", ctypes.c_double)]
+
+
+EXPORTS = ["bgpc_opts_default", "bgpc_ctx_create", "bgpc_ctx_destroy", "bgpc_color",
+           "d2gc_color", "bgpc_validate", "bgpc_color_sets", "bgpc_strerror"]
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load():
+    """Load libbgpc_gb300.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_build.LIB):
+        raise RuntimeError("libbgpc_gb300.so is not built: run "
+                           "paper_1701_02628_gb300.build.build() (or __graft_entry__.build())")
+    lib = ctypes.CDLL(_build.LIB)
+    vp = ctypes.c_void_p
+    lib.bgpc_opts_default.argtypes = [ctypes.POINTER(bgpc_opts_t)]
+    lib.bgpc_opts_default.restype = None
+    lib.bgpc_ctx_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int]
+    lib.bgpc_ctx_destroy.argtypes = [vp]
+    lib.bgpc_color.argtypes = [vp, ctypes.POINTER(bgpc_graph_t), ctypes.POINTER(bgpc_opts_t),
+                               vp, ctypes.POINTER(bgpc_stats_t), vp]
+    lib.d2gc_color.argtypes = [vp, ctypes.POINTER(bgpc_ugraph_t), ctypes.POINTER(bgpc_opts_t),
+                               vp, ctypes.POINTER(bgpc_stats_t), vp]
+    lib.bgpc_validate.argtypes = [vp, ctypes.POINTER(bgpc_graph_t), vp,
+                                  ctypes.POINTER(ctypes.c_int64), vp]
+    lib.bgpc_color_sets.argtypes = [vp, vp, ctypes.c_int32, vp, ctypes.c_int32, _c_i32p, _c_i32p,
+                                    ctypes.POINTER(ctypes.c_double),
+                                    ctypes.POINTER(ctypes.c_double), vp]
+    lib.bgpc_strerror.argtypes = [ctypes.c_int]
+    lib.bgpc_strerror.restype = ctypes.c_char_p
+    for name in ("bgpc_ctx_create", "bgpc_ctx_destroy", "bgpc_color", "d2gc_color",
+                 "bgpc_validate", "bgpc_color_sets"):
+        getattr(lib, name).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+class BgpcError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {bgpc_strerror(status)} ({status})")
+
+
+def bgpc_strerror(status: int) -> str:
+    return load().bgpc_strerror(status).decode()
+
+
+def _check(status: int, where: str) -> int:
+    if status < 0:
+        raise BgpcError(status, where)
+    return status
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if t.dtype != torch.int32 or not t.is_cuda or not t.is_contiguous():
+        raise TypeError("expected a contiguous int32 CUDA tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Context:
+    """A library context (device scratch memory) on one CUDA device."""
+
+    def __init__(self, device: int = 0):
+        lib = load()
+        h = ctypes.c_void_p()
+        _check(lib.bgpc_ctx_create(ctypes.byref(h), device), "bgpc_ctx_create")
+        self.handle = h
+        self.device = device
+
+    def close(self):
+        if self.handle:
+            load().bgpc_ctx_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+@dataclass
+class DeviceGraph:
+    """Bipartite graph with int32 CUDA tensors (see bgpc_graph_t)."""
+    n_a: int
+    n_b: int
+    a_ptr: torch.Tensor
+    a_idx: torch.Tensor
+    b_ptr: torch.Tensor
+    b_idx: torch.Tensor
+
+    @property
+    def nnz(self) -> int:
+        return int(self.a_idx.numel())
+
+    @staticmethod
+    def from_host(g, device="cuda") -> "DeviceGraph":
+        t = lambda a: torch.as_tensor(a, dtype=torch.int32).to(device).contiguous()
+        return DeviceGraph(int(g.n_a), int(g.n_b), t(g.a_ptr), t(g.a_idx), t(g.b_ptr), t(g.b_idx))
+
+    def c_struct(self) -> bgpc_graph_t:
+        return bgpc_graph_t(self.n_a, self.n_b, self.nnz, _ptr(self.a_ptr), _ptr(self.a_idx),
+                            _ptr(self.b_ptr), _ptr(self.b_idx))
+
+
+@dataclass
+class DeviceUGraph:
+    """Undirected graph with int32 CUDA tensors (see bgpc_ugraph_t)."""
+    n: int
+    ptr: torch.Tensor
+    idx: torch.Tensor
+
+    @property
+    def nnz(self) -> int:
+        return int(self.idx.numel())
+
+    @staticmethod
+    def from_host(g, device="cuda") -> "DeviceUGraph":
+        t = lambda a: torch.as_tensor(a, dtype=torch.int32).to(device).contiguous()
+        return DeviceUGraph(int(g.n), t(g.ptr), t(g.idx))
+
+    def c_struct(self) -> bgpc_ugraph_t:
+        return bgpc_ugraph_t(self.n, self.nnz, _ptr(self.ptr), _ptr(self.idx))
+
+
+def bgpc_opts_default() -> bgpc_opts_t:
+    o = bgpc_opts_t()
+    load().bgpc_opts_default(ctypes.byref(o))
+    return o
+
+
+def make_opts(policy=BGPC_FF, chunk=64, waves=16, big_net=64, rank=None, max_rounds=1000,
+              validate=False, stop_after_waves=0, W_out=None, want_balance=False,
+              profile=False) -> bgpc_opts_t:
+    o = bgpc_opts_default()
+    o.policy, o.chunk, o.waves, o.big_net = policy, chunk, waves, big_net
+    o.rank = _ptr(rank)
+    o.max_rounds = max_rounds
+    o.validate = int(bool(validate))
+    o.stop_after_waves = stop_after_waves
+    o.W_out = _ptr(W_out)
+    o.want_balance = int(bool(want_balance))
+    o.profile = int(bool(profile))
+    return o
+
+
+def stats_dict(st: bgpc_stats_t) -> dict:
+    r = min(st.rounds, BGPC_MAX_REPORT)
+    return dict(rounds=st.rounds, colors=st.colors,
+                w_per_round=list(st.w_per_round[:r]), trav_per_round=list(st.trav_per_round[:r]),
+                trav_total=st.trav_total, stopped_m=st.stopped_m, stopped_wave=st.stopped_wave,
+                n_sets=st.n_sets, max_card=st.max_card, mean_card=st.mean_card,
+                std_card=st.std_card, incid_total=st.incid_total, w_total=st.w_total,
+                kernel_launches=st.kernel_launches,
+                color_launches=st.color_launches, ms_setup=st.ms_setup, ms_color=st.ms_color,
+                ms_publish=st.ms_publish, ms_detect=st.ms_detect)
+
+
+def bgpc_color(ctx: Context, g: DeviceGraph, colors: torch.Tensor = None, stream=None, **opts):
+    """Color V_A (bgpc_color).  Returns (colors, stats dict, status)."""
+    if colors is None:
+        colors = torch.empty(g.n_a, dtype=torch.int32, device=g.a_ptr.device)
+    o = make_opts(**opts)
+    gs = g.c_struct()
+    st = bgpc_stats_t()
+    rc = load().bgpc_color(ctx.handle, ctypes.byref(gs), ctypes.byref(o), _ptr(colors),
+                           ctypes.byref(st), _stream(stream))
+    _check(rc, "bgpc_color")
+    return colors, stats_dict(st), rc
+
+
+def d2gc_color(ctx: Context, g: DeviceUGraph, colors: torch.Tensor = None, stream=None, **opts):
+    """Distance-2 coloring (d2gc_color).  Returns (colors, stats dict, status)."""
+    if colors is None:
+        colors = torch.empty(g.n, dtype=torch.int32, device=g.ptr.device)
+    o = make_opts(**opts)
+    gs = g.c_struct()
+    st = bgpc_stats_t()
+    rc = load().d2gc_color(ctx.handle, ctypes.byref(gs), ctypes.byref(o), _ptr(colors),
+                           ctypes.byref(st), _stream(stream))
+    _check(rc, "d2gc_color")
+    return colors, stats_dict(st), rc
+
+
+def bgpc_validate(ctx: Context, g: DeviceGraph, colors: torch.Tensor, stream=None) -> int:
+    """Number of V_A vertices uncolored or in conflict (bgpc_validate)."""
+    n = ctypes.c_int64(0)
+    gs = g.c_struct()
+    _check(load().bgpc_validate(ctx.handle, ctypes.byref(gs), _ptr(colors), ctypes.byref(n),
+                                _stream(stream)), "bgpc_validate")
+    return n.value
+
+
+def bgpc_color_sets(ctx: Context, colors: torch.Tensor, max_colors: int, stream=None):
+    """Color-set cardinalities and statistics (bgpc_color_sets)."""
+    card = torch.zeros(max(max_colors, 1), dtype=torch.int64, device=colors.device)
+    ns, mx = ctypes.c_int32(0), ctypes.c_int32(0)
+    mean, std = ctypes.c_double(0), ctypes.c_double(0)
+    _check(load().bgpc_color_sets(ctx.handle, _ptr(colors), colors.numel(),
+                                  ctypes.c_void_p(card.data_ptr()), max(max_colors, 1),
+                                  ctypes.byref(ns), ctypes.byref(mx), ctypes.byref(mean),
+                                  ctypes.byref(std), _stream(stream)), "bgpc_color_sets")
+    return card, dict(n_sets=ns.value, max_card=mx.value, mean_card=mean.value,
+                      std_card=std.value)

@@ -1,0 +1,509 @@
+// C ABI of the library (include/bgpc.h): argument checks, context scratch,
+// setup and the round loop of Alg. 1 (ColorWorkQueue in Q waves, then
+// RemoveConflicts, until the work queue is empty).
+#include <math.h>
+#include <string.h>
+
+#include "bgpc_internal.cuh"
+
+using namespace bgpc;
+
+namespace {
+
+struct Guard {  // restores the caller's current device
+  int prev = -1;
+  explicit Guard(int dev) {
+    cudaGetDevice(&prev);
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~Guard() {
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+int err_to_status(int32_t err) {
+  if (err & (ERR_UNSORTED | ERR_MISMATCH)) return BGPC_EUNSORTED;
+  if (err & (ERR_RANGE | ERR_RANK)) return BGPC_EINVAL;
+  if (err) return BGPC_EINTERNAL;
+  return BGPC_OK;
+}
+
+#define CU(call)                                   \
+  do {                                             \
+    cudaError_t e_ = (call);                       \
+    if (e_ != cudaSuccess) {                       \
+      cudaGetLastError();                          \
+      return e_ == cudaErrorMemoryAllocation ? BGPC_ENOMEM : BGPC_ECUDA; \
+    }                                              \
+  } while (0)
+
+int sync_scalars(bgpc_ctx_t *ctx, cudaStream_t s) {
+  CU(cudaMemcpyAsync(ctx->host, ctx->dev, sizeof(DevScalars), cudaMemcpyDeviceToHost, s));
+  CU(cudaStreamSynchronize(s));
+  return BGPC_OK;
+}
+
+int check_graph_args(const bgpc_graph_t *g) {
+  if (!g || g->n_a < 0 || g->n_b < 0 || g->nnz < 0) return BGPC_EINVAL;
+  if (g->n_a > 0 && (!g->a_ptr || !g->b_ptr)) return BGPC_EINVAL;
+  if (g->nnz > 0 && (!g->a_idx || !g->b_idx || !g->a_ptr || !g->b_ptr)) return BGPC_EINVAL;
+  if (g->n_b > 0 && !g->b_ptr) return BGPC_EINVAL;
+  return BGPC_OK;
+}
+
+int check_opts(const bgpc_opts_t *o) {
+  if (!o) return BGPC_EINVAL;
+  if (o->policy < BGPC_FF || o->policy > BGPC_B2X) return BGPC_EINVAL;
+  if (o->chunk < 1 || o->chunk > kMaxChunk) return BGPC_EINVAL;
+  if (o->waves < 1 || o->big_net < 0 || o->max_rounds < 1 || o->stop_after_waves < 0)
+    return BGPC_EINVAL;
+  return BGPC_OK;
+}
+
+// Validate a CSR: pointer array first (so that row checks stay in bounds).
+int validate_csr(bgpc_ctx_t *ctx, const int32_t *ptr, const int32_t *idx, int32_t n,
+                 int32_t nnz, int32_t bound, cudaStream_t s) {
+  CU(cudaMemsetAsync(&ctx->dev->err, 0, sizeof(int32_t), s));
+  launch_check_ptr(ptr, n, nnz, &ctx->dev->err, s);
+  int rc = sync_scalars(ctx, s);
+  if (rc) return rc;
+  if (ctx->host->err) return err_to_status(ctx->host->err);
+  launch_check_rows(ptr, idx, n, bound, &ctx->dev->err, ctx->num_sms, s);
+  rc = sync_scalars(ctx, s);
+  if (rc) return rc;
+  return err_to_status(ctx->host->err);
+}
+
+int32_t round_up16(int64_t x) { return (int32_t)((x + 15) & ~(int64_t)15); }
+
+// Phase timing with CUDA events recorded on the launch stream (opts.profile).
+enum Phase { PH_SETUP = 0, PH_COLOR = 1, PH_PUBLISH = 2, PH_DETECT = 3 };
+struct PhaseTimer {
+  bgpc_ctx_t *ctx;
+  cudaStream_t s;
+  bool on;
+  int used = 0;
+  std::vector<int> phase;
+  double ms[4] = {0, 0, 0, 0};
+  PhaseTimer(bgpc_ctx_t *c, cudaStream_t st, bool enabled) : ctx(c), s(st), on(enabled) {}
+  cudaEvent_t ev(int i) {
+    while ((int)ctx->events.size() <= i) {
+      cudaEvent_t e;
+      cudaEventCreate(&e);
+      ctx->events.push_back(e);
+    }
+    return ctx->events[i];
+  }
+  int begin() {
+    if (!on) return -1;
+    int i = used;
+    cudaEventRecord(ev(i), s);
+    used += 2;
+    return i;
+  }
+  void end(int i, int ph) {
+    if (!on || i < 0) return;
+    cudaEventRecord(ev(i + 1), s);
+    if ((int)phase.size() <= i / 2) phase.resize(i / 2 + 1);
+    phase[i / 2] = ph;
+  }
+  // after the stream has been synchronised
+  void collect() {
+    if (!on) return;
+    for (int k = 0; k < used / 2; k++) {
+      float t = 0.f;
+      if (cudaEventElapsedTime(&t, ctx->events[2 * k], ctx->events[2 * k + 1]) == cudaSuccess)
+        ms[phase[k]] += t;
+      else
+        cudaGetLastError();
+    }
+    used = 0;
+  }
+};
+
+int ensure_table(bgpc_ctx_t *ctx, size_t entries, cudaStream_t s, int64_t *nk) {
+  if (entries > ctx->dtab.cap) {
+    CU(grow(ctx->dtab, entries));
+    ctx->dtab_filled = 0;
+  }
+  if (entries > ctx->dtab_filled) {
+    *nk += launch_fill(ctx->dtab.p, ctx->dtab.cap, INT32_MAX, s);
+    ctx->dtab_filled = ctx->dtab.cap;
+  }
+  return BGPC_OK;
+}
+
+int color_impl(bgpc_ctx_t *ctx, const bgpc_graph_t &g, const bgpc_opts_t &o, int32_t *colors,
+               bgpc_stats_t *stats, cudaStream_t s) {
+  bgpc_stats_t st;
+  memset(&st, 0, sizeof(st));
+  const int32_t n_a = g.n_a, n_b = g.n_b, nnz = g.nnz;
+  const int sms = ctx->num_sms;
+  if (n_a == 0) {
+    if (stats) *stats = st;
+    return BGPC_OK;
+  }
+  int rc;
+  if (o.validate) {
+    if ((rc = validate_csr(ctx, g.a_ptr, g.a_idx, n_a, nnz, n_b, s))) return rc;
+    if ((rc = validate_csr(ctx, g.b_ptr, g.b_idx, n_b, nnz, n_a, s))) return rc;
+  }
+  const size_t nz = (size_t)(nnz > 0 ? nnz : 1);
+  CU(grow(ctx->tpos, nz));
+  CU(grow(ctx->nc, nz));
+  CU(grow(ctx->npos, nz));
+  CU(grow(ctx->nown, nz));
+  CU(grow(ctx->s_own, (size_t)n_a));
+  CU(grow(ctx->d2tot, (size_t)n_a));
+  CU(grow(ctx->W0, (size_t)n_a));
+  CU(grow(ctx->W1, (size_t)n_a));
+  CU(grow(ctx->kofs, (size_t)n_a));
+  CU(grow(ctx->stage, (size_t)n_a));
+  CU(grow(ctx->newpos, (size_t)n_a));
+  CU(grow(ctx->lose, (size_t)n_a));
+  CU(grow(ctx->blocksum, (size_t)div_up(n_a, 4096) + 1));
+  CU(grow(ctx->bigt, (size_t)(n_b > 0 ? n_b : 1)));
+  CU(grow(ctx->bigd, (size_t)(n_b > 0 ? n_b : 1)));
+
+  // ---- setup (Alg. 1: W <- V_color, c <- -1), static graph analysis
+  PhaseTimer tm(ctx, s, o.profile != 0);
+  int64_t nk = 0;
+  int ev = tm.begin();
+  CU(cudaMemsetAsync(ctx->dev, 0, sizeof(DevScalars), s));
+  CU(cudaMemsetAsync(&ctx->dev->gmax, 0xff, sizeof(int32_t), s));
+  CU(cudaMemsetAsync(ctx->lose.p, 0, (size_t)n_a, s));
+  nk += launch_tpos(g, ctx->tpos.p, &ctx->dev->err, sms, s);
+  nk += launch_vertex_static(g, ctx->tpos.p, ctx->s_own.p, ctx->d2tot.p, ctx->nown.p, sms, s);
+  nk += launch_net_static(g, o.big_net, ctx->bigt.p, ctx->bigd.p, ctx->dev, s);
+  nk += launch_init_queue(o.rank, n_a, ctx->W0.p, &ctx->dev->err, s);
+  nk += launch_init_mirror(g, o.rank, ctx->tpos.p, ctx->nc.p, ctx->npos.p, colors, sms, s);
+  tm.end(ev, PH_SETUP);
+  CU(cudaGetLastError());
+  if ((rc = sync_scalars(ctx, s))) return rc;
+  tm.collect();
+  if (ctx->host->err) return err_to_status(ctx->host->err);
+  const int32_t nbig_t = ctx->host->nbig_t, nbig_d = ctx->host->nbig_d;
+  const int32_t maxnet = ctx->host->maxnet;
+  const int32_t max_cbw = wave_max_cbw(ctx->smem_optin);
+
+  int32_t *W = ctx->W0.p, *Wn = ctx->W1.p;
+  int32_t m = n_a, gmax = -1, r = 0;
+  int64_t waves_done = 0;
+  const int32_t C = o.chunk, Q = o.waves;
+  while (m > 0) {
+    if (r >= o.max_rounds) return BGPC_EROUNDS;
+    // every color of this round is <= max(gmax, maxnet - 1, 0) + C * Q
+    const int64_t b0 = (int64_t)(gmax > maxnet - 1 ? gmax : maxnet - 1);
+    const int64_t cbw64 = (b0 > 0 ? b0 : 0) + (int64_t)C * Q + C + 2;
+    if (cbw64 > max_cbw) return BGPC_ENOMEM;
+    const int32_t cbw = round_up16(cbw64);
+    const int32_t nslots = nbig_d < 2 * sms ? (nbig_d > 0 ? nbig_d : 1) : 2 * sms;
+    if ((rc = ensure_table(ctx, (size_t)nslots * (size_t)cbw, s, &nk))) return rc;
+
+    ev = tm.begin();
+    if (nbig_t > 0)
+      nk += launch_kofs(g.b_ptr, ctx->nc.p, ctx->npos.p, ctx->nown.p, ctx->bigt.p, nbig_t,
+                        ctx->kofs.p, sms, s);
+    CU(cudaMemsetAsync(&ctx->dev->trav, 0, 2 * sizeof(unsigned long long), s));
+    nk += launch_trav(g.a_ptr, W, ctx->d2tot.p, m, ctx->dev, s);
+    tm.end(ev, PH_DETECT);
+
+    // chunks of every wave (a pure function of nch and Q), uploaded once per round
+    const int64_t nch = ((int64_t)m + C - 1) / C;
+    std::vector<int64_t> woff((size_t)Q + 1, 0);
+    {
+      if ((size_t)nch > ctx->h_wlist_cap) {
+        if (ctx->h_wlist) cudaFreeHost(ctx->h_wlist);
+        ctx->h_wlist = nullptr;
+        ctx->h_wlist_cap = 0;
+        CU(cudaMallocHost((void **)&ctx->h_wlist, sizeof(int32_t) * (size_t)nch));
+        ctx->h_wlist_cap = (size_t)nch;
+      }
+      CU(grow(ctx->wlist, (size_t)nch));
+      for (int64_t j = 0; j < nch; j++) woff[(size_t)wave_of(j, Q) + 1]++;
+      for (int32_t q = 0; q < Q; q++) woff[q + 1] += woff[q];
+      std::vector<int64_t> fill(woff.begin(), woff.end());
+      for (int64_t j = 0; j < nch; j++) ctx->h_wlist[fill[(size_t)wave_of(j, Q)]++] = (int32_t)j;
+      CU(cudaMemcpyAsync(ctx->wlist.p, ctx->h_wlist, sizeof(int32_t) * (size_t)nch,
+                         cudaMemcpyHostToDevice, s));
+    }
+    for (int32_t q = 0; q < Q; q++) {
+      if (o.stop_after_waves > 0 && waves_done == o.stop_after_waves) {
+        if (o.W_out) CU(cudaMemcpyAsync(o.W_out, W, sizeof(int32_t) * (size_t)m,
+                                        cudaMemcpyDeviceToDevice, s));
+        CU(cudaStreamSynchronize(s));
+        tm.collect();
+        st.rounds = r + 1;
+        st.stopped_m = m;
+        st.stopped_wave = q;
+        st.colors = gmax + 1;
+        if (stats) *stats = st;
+        return BGPC_STOPPED;
+      }
+      const int32_t *wchunks = ctx->wlist.p + woff[q];
+      const int32_t nwave = (int32_t)(woff[q + 1] - woff[q]);
+      if (nwave > 0) {
+        WaveArgs a;
+        a.a_ptr = g.a_ptr;
+        a.a_idx = g.a_idx;
+        a.b_ptr = g.b_ptr;
+        a.nc = ctx->nc.p;
+        a.W = W;
+        a.kofs = ctx->kofs.p;
+        a.s_own = ctx->s_own.p;
+        a.d2tot = ctx->d2tot.p;
+        a.stage = ctx->stage.p;
+        a.dev = ctx->dev;
+        a.err = &ctx->dev->err;
+        a.m = m;
+        a.C = C;
+        a.T = o.big_net;
+        a.chunks = wchunks;
+        a.nchunks = nwave;
+        a.maxnet = maxnet;
+        a.cbw = cbw;
+        ev = tm.begin();
+        CU(launch_color_wave(o.policy, a, sms, ctx->smem_optin, s));
+        tm.end(ev, PH_COLOR);
+        nk++;
+        st.color_launches++;
+        ev = tm.begin();
+        nk += launch_publish(g.a_ptr, ctx->tpos.p, W, ctx->stage.p, wchunks, nwave, C, m,
+                             ctx->nc.p, colors, ctx->dev, sms, s);
+        tm.end(ev, PH_PUBLISH);
+      }
+      waves_done++;
+    }
+    // ---- RemoveConflicts and the next work queue
+    ev = tm.begin();
+    nk += launch_detect(g.b_ptr, n_b, ctx->nc.p, ctx->npos.p, ctx->bigd.p, nbig_d, ctx->dtab.p,
+                        cbw, nslots, ctx->lose.p, sms, s);
+    nk += launch_compact(ctx->lose.p, W, m, ctx->newpos.p, Wn, ctx->blocksum.p, ctx->dev, s);
+    nk += launch_relabel(g.a_ptr, ctx->tpos.p, W, m, ctx->lose.p, ctx->newpos.p, ctx->nc.p,
+                         ctx->npos.p, colors, sms, s);
+    nk += launch_gmax(colors, n_a, ctx->dev, s);
+    tm.end(ev, PH_DETECT);
+    CU(cudaGetLastError());
+    if ((rc = sync_scalars(ctx, s))) return rc;
+    tm.collect();
+    if (ctx->host->err) return err_to_status(ctx->host->err);
+    if (r < BGPC_MAX_REPORT) {
+      st.w_per_round[r] = m;
+      st.trav_per_round[r] = (int64_t)ctx->host->trav;
+    }
+    st.trav_total += (int64_t)ctx->host->trav;
+    st.incid_total += (int64_t)ctx->host->incid;
+    st.w_total += m;
+    r++;
+    const int32_t mn = ctx->host->m_next;
+    if (mn < 0 || mn > m) return BGPC_EINTERNAL;
+    int32_t *t = W;
+    W = Wn;
+    Wn = t;
+    m = mn;
+    gmax = ctx->host->gmax;
+  }
+  st.rounds = r;
+  st.colors = gmax + 1;
+  if (o.want_balance && gmax >= 0) {
+    CU(grow(ctx->card, (size_t)gmax + 1));
+    nk += launch_card(colors, n_a, ctx->card.p, gmax + 1, &ctx->dev->err, s);
+    nk += launch_card_stats(ctx->card.p, gmax + 1, ctx->dev, s);
+    if ((rc = sync_scalars(ctx, s))) return rc;
+    if (ctx->host->err) return err_to_status(ctx->host->err);
+    const double sets = (double)ctx->host->acc[0];
+    st.n_sets = (int32_t)ctx->host->acc[0];
+    st.max_card = (int32_t)ctx->host->acc[1];
+    st.mean_card = sets > 0 ? (double)ctx->host->acc[2] / sets : 0.0;
+    const double ex2 = sets > 0 ? (double)ctx->host->acc[3] / sets : 0.0;
+    const double var = ex2 - st.mean_card * st.mean_card;
+    st.std_card = var > 0 ? sqrt(var) : 0.0;
+  }
+  st.kernel_launches = nk;
+  st.ms_setup = tm.ms[PH_SETUP];
+  st.ms_color = tm.ms[PH_COLOR];
+  st.ms_publish = tm.ms[PH_PUBLISH];
+  st.ms_detect = tm.ms[PH_DETECT];
+  if (stats) *stats = st;
+  return BGPC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void bgpc_opts_default(bgpc_opts_t *o) {
+  if (!o) return;
+  memset(o, 0, sizeof(*o));
+  o->policy = BGPC_FF;
+  o->chunk = 64;
+  o->waves = 16;
+  o->big_net = 64;
+  o->rank = nullptr;
+  o->max_rounds = 1000;
+  o->validate = 0;
+  o->stop_after_waves = 0;
+  o->W_out = nullptr;
+  o->want_balance = 0;
+}
+
+int bgpc_ctx_create(bgpc_ctx_t **out, int device) {
+  if (!out) return BGPC_EINVAL;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+    cudaGetLastError();
+    return BGPC_EINVAL;
+  }
+  Guard guard(device);
+  bgpc_ctx_t *ctx = new bgpc_ctx_t();
+  ctx->device = device;
+  if (cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device) !=
+          cudaSuccess ||
+      cudaDeviceGetAttribute(&ctx->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin,
+                             device) != cudaSuccess ||
+      cudaMalloc((void **)&ctx->dev, sizeof(DevScalars)) != cudaSuccess ||
+      cudaMallocHost((void **)&ctx->host, sizeof(DevScalars)) != cudaSuccess) {
+    cudaGetLastError();
+    bgpc_ctx_destroy(ctx);
+    return BGPC_ECUDA;
+  }
+  *out = ctx;
+  return BGPC_OK;
+}
+
+int bgpc_ctx_destroy(bgpc_ctx_t *ctx) {
+  if (!ctx) return BGPC_OK;
+  Guard guard(ctx->device);
+  cudaDeviceSynchronize();
+  release(ctx->tpos); release(ctx->nc); release(ctx->npos); release(ctx->nown);
+  release(ctx->s_own); release(ctx->d2tot); release(ctx->W0); release(ctx->W1);
+  release(ctx->kofs); release(ctx->stage); release(ctx->newpos); release(ctx->lose);
+  release(ctx->blocksum); release(ctx->bigt); release(ctx->bigd);
+  release(ctx->cptr); release(ctx->cidx); release(ctx->dtab); release(ctx->vtab);
+  release(ctx->wlist);
+  if (ctx->h_wlist) cudaFreeHost(ctx->h_wlist);
+  release(ctx->card); release(ctx->bad);
+  for (cudaEvent_t e : ctx->events) cudaEventDestroy(e);
+  ctx->events.clear();
+  if (ctx->dev) cudaFree(ctx->dev);
+  if (ctx->host) cudaFreeHost(ctx->host);
+  delete ctx;
+  return BGPC_OK;
+}
+
+int bgpc_color(bgpc_ctx_t *ctx, const bgpc_graph_t *g, const bgpc_opts_t *opts, int32_t *colors,
+               bgpc_stats_t *stats, void *stream) {
+  if (!ctx) return BGPC_EINVAL;
+  int rc = check_graph_args(g);
+  if (rc) return rc;
+  if ((rc = check_opts(opts))) return rc;
+  if (g->n_a > 0 && !colors) return BGPC_EINVAL;
+  Guard guard(ctx->device);
+  return color_impl(ctx, *g, *opts, colors, stats, (cudaStream_t)stream);
+}
+
+int d2gc_color(bgpc_ctx_t *ctx, const bgpc_ugraph_t *g, const bgpc_opts_t *opts, int32_t *colors,
+               bgpc_stats_t *stats, void *stream) {
+  if (!ctx || !g || g->n < 0 || g->nnz < 0) return BGPC_EINVAL;
+  if (g->n > 0 && (!g->ptr || !colors)) return BGPC_EINVAL;
+  if (g->nnz > 0 && !g->idx) return BGPC_EINVAL;
+  if ((int64_t)g->nnz + g->n >= INT32_MAX) return BGPC_EINVAL;
+  int rc = check_opts(opts);
+  if (rc) return rc;
+  Guard guard(ctx->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  if (opts->validate && g->n > 0) {
+    if ((rc = validate_csr(ctx, g->ptr, g->idx, g->n, g->nnz, g->n, s))) return rc;
+  }
+  const int32_t cn = g->nnz + g->n;
+  CU(grow(ctx->cptr, (size_t)g->n + 1));
+  CU(grow(ctx->cidx, (size_t)(cn > 0 ? cn : 1)));
+  launch_closed_nbhd(*g, ctx->cptr.p, ctx->cidx.p, ctx->num_sms, s);
+  CU(cudaGetLastError());
+  bgpc_graph_t bg;
+  bg.n_a = g->n;
+  bg.n_b = g->n;
+  bg.nnz = cn;
+  bg.a_ptr = ctx->cptr.p;
+  bg.a_idx = ctx->cidx.p;
+  bg.b_ptr = ctx->cptr.p;
+  bg.b_idx = ctx->cidx.p;
+  bgpc_opts_t o = *opts;
+  return color_impl(ctx, bg, o, colors, stats, s);
+}
+
+int bgpc_validate(bgpc_ctx_t *ctx, const bgpc_graph_t *g, const int32_t *colors, int64_t *n_bad,
+                  void *stream) {
+  if (!ctx || !n_bad) return BGPC_EINVAL;
+  int rc = check_graph_args(g);
+  if (rc) return rc;
+  if (g->n_a > 0 && !colors) return BGPC_EINVAL;
+  Guard guard(ctx->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  *n_bad = 0;
+  if (g->n_a == 0) return BGPC_OK;
+  CU(grow(ctx->bigt, (size_t)(g->n_b > 0 ? g->n_b : 1)));
+  CU(grow(ctx->bigd, (size_t)(g->n_b > 0 ? g->n_b : 1)));
+  CU(grow(ctx->bad, (size_t)g->n_a));
+  CU(cudaMemsetAsync(ctx->dev, 0, sizeof(DevScalars), s));
+  launch_net_static(*g, INT32_MAX, ctx->bigt.p, ctx->bigd.p, ctx->dev, s);
+  launch_gmax(colors, g->n_a, ctx->dev, s);
+  if ((rc = sync_scalars(ctx, s))) return rc;
+  const int32_t tabcap = ctx->host->gmax + 1 > 0 ? ctx->host->gmax + 1 : 1;
+  const int32_t nbig_d = ctx->host->nbig_d;
+  const int32_t nslots = nbig_d < 2 * ctx->num_sms ? (nbig_d > 0 ? nbig_d : 1) : 2 * ctx->num_sms;
+  const size_t need = (size_t)nslots * (size_t)tabcap;
+  if (need > ctx->vtab.cap) {
+    CU(grow(ctx->vtab, need));
+    CU(cudaMemsetAsync(ctx->vtab.p, 0, ctx->vtab.cap * sizeof(int32_t), s));
+  }
+  launch_validate(*g, colors, ctx->bigd.p, nbig_d, ctx->vtab.p, tabcap, nslots, ctx->bad.p,
+                  ctx->dev, ctx->num_sms, s);
+  CU(cudaGetLastError());
+  if ((rc = sync_scalars(ctx, s))) return rc;
+  *n_bad = (int64_t)ctx->host->acc[0];
+  return BGPC_OK;
+}
+
+int bgpc_color_sets(bgpc_ctx_t *ctx, const int32_t *colors, int32_t n, int64_t *card,
+                    int32_t max_colors, int32_t *n_sets, int32_t *max_card, double *mean_card,
+                    double *std_card, void *stream) {
+  if (!ctx || n < 0 || max_colors < 1 || !card || (n > 0 && !colors)) return BGPC_EINVAL;
+  Guard guard(ctx->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  CU(cudaMemsetAsync(&ctx->dev->err, 0, sizeof(int32_t), s));
+  launch_card(colors, n, (unsigned long long *)card, max_colors, &ctx->dev->err, s);
+  launch_card_stats((const unsigned long long *)card, max_colors, ctx->dev, s);
+  CU(cudaGetLastError());
+  int rc = sync_scalars(ctx, s);
+  if (rc) return rc;
+  if (ctx->host->err) return BGPC_EINVAL;
+  const double sets = (double)ctx->host->acc[0];
+  const double mean = sets > 0 ? (double)ctx->host->acc[2] / sets : 0.0;
+  const double var = sets > 0 ? (double)ctx->host->acc[3] / sets - mean * mean : 0.0;
+  if (n_sets) *n_sets = (int32_t)ctx->host->acc[0];
+  if (max_card) *max_card = (int32_t)ctx->host->acc[1];
+  if (mean_card) *mean_card = mean;
+  if (std_card) *std_card = var > 0 ? sqrt(var) : 0.0;
+  return BGPC_OK;
+}
+
+const char *bgpc_strerror(int status) {
+  switch (status) {
+    case BGPC_OK: return "ok";
+    case BGPC_STOPPED: return "stopped after the requested number of waves";
+    case BGPC_EINVAL: return "invalid argument";
+    case BGPC_ENOMEM: return "out of device memory or on-chip capacity";
+    case BGPC_ECUDA: return "CUDA runtime error";
+    case BGPC_EROUNDS: return "round limit exceeded";
+    case BGPC_ETIMEOUT: return "a bounded device wait timed out";
+    case BGPC_EUNSORTED: return "adjacency not sorted/unique or CSR and CSC disagree";
+    case BGPC_EINTERNAL: return "internal consistency check failed";
+    default: return "unknown status";
+  }
+}
+
+}  // extern "C"

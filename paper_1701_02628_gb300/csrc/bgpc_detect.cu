@@ -1,0 +1,337 @@
+// RemoveConflicts and the per-round bookkeeping of Alg. 1:
+//  * reverse first-fit offsets k for the owners of big nets (Alg. 8's W_local
+//    order, restricted to vertices still in W that own the net),
+//  * per-net conflict detection (Alg. 7's traversal) with the lower-rank-wins
+//    rule of Alg. 3: among members of W_r sharing a color in a net, all but
+//    the lowest position lose,
+//  * rank-ordered compaction of the losers into W_{r+1} (prefix sums, no
+//    order-dependent atomics) and the relabelling of the net-major mirrors.
+#include "bgpc_internal.cuh"
+
+namespace bgpc {
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kNT = 256;
+constexpr int kScanNT = 1024;
+constexpr int kScanPer = 4;
+constexpr int kScanTile = kScanNT * kScanPer;
+
+template <int NT>
+__device__ __forceinline__ int32_t block_excl_scan(int32_t v, int32_t *red, int32_t *total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int32_t inc = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    int32_t y = __shfl_up_sync(kFull, inc, o);
+    if (lane >= o) inc += y;
+  }
+  if (lane == 31) red[warp] = inc;
+  __syncthreads();
+  int32_t before = 0, tot = 0;
+#pragma unroll
+  for (int i = 0; i < NT / 32; i++) {
+    int32_t r = red[i];
+    before += (i < warp) ? r : 0;
+    tot += r;
+  }
+  __syncthreads();
+  *total = tot;
+  return before + inc - v;
+}
+
+// k for each owner of a net with |vtxs| > T that is in W: the number of
+// members before it in vtxs order that are in W and own the same net.
+__global__ void __launch_bounds__(kNT) k_kofs(const int32_t *__restrict__ b_ptr,
+                                              const int32_t *__restrict__ npos,
+                                              const uint8_t *__restrict__ nown,
+                                              const int32_t *__restrict__ bigt, int32_t nbig,
+                                              int32_t *__restrict__ kofs) {
+  __shared__ int32_t red[kNT / 32];
+  for (int32_t b = blockIdx.x; b < nbig; b += gridDim.x) {
+    const int32_t v = bigt[b];
+    const int32_t beg = b_ptr[v], end = b_ptr[v + 1];
+    int32_t carry = 0;
+    for (int32_t t0 = beg; t0 < end; t0 += kNT) {
+      const int32_t f = t0 + (int32_t)threadIdx.x;
+      int32_t pos = -1, flag = 0;
+      if (f < end) {
+        pos = npos[f];
+        flag = (pos >= 0 && nown[f]) ? 1 : 0;
+      }
+      int32_t total;
+      int32_t ex = block_excl_scan<kNT>(flag, red, &total);
+      if (flag) kofs[pos] = carry + ex;
+      carry += total;
+    }
+  }
+}
+
+__global__ void k_trav(const int32_t *__restrict__ a_ptr, const int32_t *__restrict__ W,
+                       const int32_t *__restrict__ d2tot, int32_t m, DevScalars *dev) {
+  unsigned long long acc = 0, inc = 0;
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < m;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t w = W[p];
+    const int32_t deg = a_ptr[w + 1] - a_ptr[w];
+    acc += (unsigned long long)(d2tot[w] - deg);
+    inc += (unsigned long long)deg;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    acc += __shfl_xor_sync(kFull, acc, o);
+    inc += __shfl_xor_sync(kFull, inc, o);
+  }
+  if ((threadIdx.x & 31) == 0 && acc) atomicAdd(&dev->trav, acc);
+  if ((threadIdx.x & 31) == 0 && inc) atomicAdd(&dev->incid, inc);
+}
+
+// Warp tier: one warp per net with at most 32 members.  Members outside W
+// never share a color with a W member (their colors were forbidden), so
+// only W members take part; a member loses when a member of its color
+// class has a smaller position.
+__global__ void k_detect_warp(const int32_t *__restrict__ b_ptr, int32_t n_b,
+                              const int32_t *__restrict__ nc, const int32_t *__restrict__ npos,
+                              uint8_t *__restrict__ lose) {
+  const int lane = threadIdx.x & 31;
+  int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t v = warp; v < n_b; v += nwarps) {
+    const int32_t beg = b_ptr[v], size = b_ptr[v + 1] - beg;
+    if (size < 2 || size > kDetectWarpMax) continue;
+    int32_t pos = -1, col = -1 - lane;  // unique dummies for inactive lanes
+    if (lane < size) {
+      pos = npos[beg + lane];
+      if (pos >= 0) col = nc[beg + lane];
+    }
+    const unsigned grp = __match_any_sync(kFull, col);
+    int32_t minpos = (pos >= 0) ? pos : INT32_MAX;
+#pragma unroll
+    for (int k = 0; k < 32; k++) {
+      int32_t pk = __shfl_sync(kFull, pos, k);
+      if (((grp >> k) & 1u) && pk >= 0 && pk < minpos) minpos = pk;
+    }
+    if (pos >= 0 && minpos < pos) lose[pos] = 1;
+  }
+}
+
+// Table tier: one CTA per net with more than 32 members; a per-CTA table
+// indexed by color holds the smallest W position of that color in the net
+// (all entries INT32_MAX between nets).
+__global__ void __launch_bounds__(kNT) k_detect_table(const int32_t *__restrict__ b_ptr,
+                                                      const int32_t *__restrict__ nc,
+                                                      const int32_t *__restrict__ npos,
+                                                      const int32_t *__restrict__ bigd,
+                                                      int32_t nbig, int32_t *__restrict__ dtab,
+                                                      int32_t tabcap, uint8_t *__restrict__ lose) {
+  int32_t *tab = dtab + (size_t)blockIdx.x * (size_t)tabcap;
+  for (int32_t b = blockIdx.x; b < nbig; b += gridDim.x) {
+    const int32_t v = bigd[b];
+    const int32_t beg = b_ptr[v], end = b_ptr[v + 1];
+    for (int32_t f = beg + threadIdx.x; f < end; f += kNT) {
+      const int32_t pos = npos[f];
+      if (pos >= 0) {
+        const int32_t c = nc[f];
+        if (c >= 0 && c < tabcap) atomicMin(&tab[c], pos);
+      }
+    }
+    __syncthreads();
+    for (int32_t f = beg + threadIdx.x; f < end; f += kNT) {
+      const int32_t pos = npos[f];
+      if (pos >= 0) {
+        const int32_t c = nc[f];
+        if (c >= 0 && c < tabcap && tab[c] < pos) lose[pos] = 1;
+      }
+    }
+    __syncthreads();
+    for (int32_t f = beg + threadIdx.x; f < end; f += kNT) {
+      const int32_t pos = npos[f];
+      if (pos >= 0) {
+        const int32_t c = nc[f];
+        if (c >= 0 && c < tabcap) tab[c] = INT32_MAX;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ----------------------------------------------------------- compaction
+__global__ void __launch_bounds__(kScanNT) k_scan_count(const uint8_t *__restrict__ lose,
+                                                        int32_t m, int32_t *__restrict__ blocksum) {
+  __shared__ int32_t red[kScanNT / 32];
+  const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanPer;
+  int32_t c = 0;
+#pragma unroll
+  for (int q = 0; q < kScanPer; q++) c += (base + q < m) ? lose[base + q] : 0;
+  int32_t total;
+  block_excl_scan<kScanNT>(c, red, &total);
+  if (threadIdx.x == 0) blocksum[blockIdx.x] = total;
+}
+
+__global__ void __launch_bounds__(kScanNT) k_scan_blocks(int32_t *__restrict__ blocksum,
+                                                         int32_t nblocks, DevScalars *dev) {
+  __shared__ int32_t red[kScanNT / 32];
+  int32_t carry = 0;
+  for (int32_t b0 = 0; b0 < nblocks; b0 += kScanNT) {
+    const int32_t b = b0 + (int32_t)threadIdx.x;
+    const int32_t x = (b < nblocks) ? blocksum[b] : 0;
+    int32_t total;
+    const int32_t ex = block_excl_scan<kScanNT>(x, red, &total);
+    if (b < nblocks) blocksum[b] = carry + ex;
+    carry += total;
+  }
+  if (threadIdx.x == 0) dev->m_next = carry;
+}
+
+__global__ void __launch_bounds__(kScanNT) k_scan_scatter(const uint8_t *__restrict__ lose,
+                                                          const int32_t *__restrict__ W,
+                                                          int32_t m,
+                                                          const int32_t *__restrict__ blocksum,
+                                                          int32_t *__restrict__ newpos,
+                                                          int32_t *__restrict__ Wn) {
+  __shared__ int32_t red[kScanNT / 32];
+  const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanPer;
+  int32_t f[kScanPer];
+  int32_t c = 0;
+#pragma unroll
+  for (int q = 0; q < kScanPer; q++) {
+    f[q] = (base + q < m) ? lose[base + q] : 0;
+    c += f[q];
+  }
+  int32_t total;
+  int32_t ex = block_excl_scan<kScanNT>(c, red, &total) + blocksum[blockIdx.x];
+#pragma unroll
+  for (int q = 0; q < kScanPer; q++) {
+    if (f[q]) {
+      newpos[base + q] = ex;
+      Wn[ex] = W[base + q];
+      ex++;
+    }
+  }
+}
+
+// Losers: uncolored again, and their nc / npos entries carry the new
+// position; winners leave W (npos = -1).  Clears the lose flags.
+__global__ void k_relabel(const int32_t *__restrict__ a_ptr, const int32_t *__restrict__ tpos,
+                          const int32_t *__restrict__ W, int32_t m, uint8_t *__restrict__ lose,
+                          const int32_t *__restrict__ newpos, int32_t *__restrict__ nc,
+                          int32_t *__restrict__ npos, int32_t *__restrict__ colors) {
+  const int lane = threadIdx.x & 31;
+  int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t p = warp; p < m; p += nwarps) {
+    const int32_t w = W[p];
+    const bool l = lose[p] != 0;
+    const int32_t np = l ? newpos[p] : -1;
+    const int32_t beg = a_ptr[w], end = a_ptr[w + 1];
+    for (int32_t i = beg + lane; i < end; i += 32) {
+      const int32_t f = tpos[i];
+      npos[f] = np;
+      if (l) nc[f] = -2 - np;
+    }
+    __syncwarp();
+    if (lane == 0) {
+      if (l) colors[w] = -1;
+      lose[p] = 0;
+    }
+  }
+}
+
+__global__ void k_gmax(const int32_t *__restrict__ colors, int32_t n, DevScalars *dev) {
+  int32_t mx = -1;
+  for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n;
+       u += (int64_t)gridDim.x * blockDim.x)
+    mx = max(mx, colors[u]);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(kFull, mx, o));
+  if ((threadIdx.x & 31) == 0 && mx >= 0) atomicMax(&dev->gmax, mx);
+}
+
+__global__ void k_fill(int32_t *p, size_t n, int32_t v) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x)
+    p[i] = v;
+}
+
+inline int warps_grid(long long items, int sms) {
+  long long g = div_up(items * 32, kNT);
+  long long cap = (long long)sms * 16;
+  if (g > cap) g = cap;
+  if (g < 1) g = 1;
+  return (int)g;
+}
+
+}  // namespace
+
+int launch_kofs(const int32_t *b_ptr, const int32_t *, const int32_t *npos, const uint8_t *nown,
+                 const int32_t *bigt, int32_t nbig, int32_t *kofs, int sms, cudaStream_t s) {
+  if (nbig <= 0) return 0;
+  int grid = nbig < sms * 8 ? nbig : sms * 8;
+  k_kofs<<<grid, kNT, 0, s>>>(b_ptr, npos, nown, bigt, nbig, kofs);
+  return 1;
+}
+
+int launch_trav(const int32_t *a_ptr, const int32_t *W, const int32_t *d2tot, int32_t m,
+                 DevScalars *dev, cudaStream_t s) {
+  if (m <= 0) return 0;
+  int grid = div_up(m, kNT);
+  if (grid > 1184) grid = 1184;
+  k_trav<<<grid, kNT, 0, s>>>(a_ptr, W, d2tot, m, dev);
+  return 1;
+}
+
+int launch_detect(const int32_t *b_ptr, int32_t n_b, const int32_t *nc, const int32_t *npos,
+                   const int32_t *bigd, int32_t nbigd, int32_t *dtab, int32_t tabcap,
+                   int32_t nslots, uint8_t *lose, int sms, cudaStream_t s) {
+  int n = 0;
+  if (n_b > 0) {
+    k_detect_warp<<<warps_grid(n_b, sms), kNT, 0, s>>>(b_ptr, n_b, nc, npos, lose);
+    n++;
+  }
+  if (nbigd > 0) {
+    int grid = nbigd < nslots ? nbigd : nslots;
+    k_detect_table<<<grid, kNT, 0, s>>>(b_ptr, nc, npos, bigd, nbigd, dtab, tabcap, lose);
+    n++;
+  }
+  return n;
+}
+
+int launch_compact(const uint8_t *lose, const int32_t *W, int32_t m, int32_t *newpos,
+                    int32_t *Wn, int32_t *blocksum, DevScalars *dev, cudaStream_t s) {
+  const int nblocks = div_up(m, kScanTile);
+  if (m <= 0) {
+    cudaMemsetAsync(&dev->m_next, 0, sizeof(int32_t), s);
+    return 0;
+  }
+  k_scan_count<<<nblocks, kScanNT, 0, s>>>(lose, m, blocksum);
+  k_scan_blocks<<<1, kScanNT, 0, s>>>(blocksum, nblocks, dev);
+  k_scan_scatter<<<nblocks, kScanNT, 0, s>>>(lose, W, m, blocksum, newpos, Wn);
+  return 3;
+}
+
+int launch_relabel(const int32_t *a_ptr, const int32_t *tpos, const int32_t *W, int32_t m,
+                    uint8_t *lose, const int32_t *newpos, int32_t *nc, int32_t *npos,
+                    int32_t *colors, int sms, cudaStream_t s) {
+  if (m <= 0) return 0;
+  k_relabel<<<warps_grid(m, sms), kNT, 0, s>>>(a_ptr, tpos, W, m, lose, newpos, nc, npos, colors);
+  return 1;
+}
+
+int launch_gmax(const int32_t *colors, int32_t n, DevScalars *dev, cudaStream_t s) {
+  cudaMemsetAsync(&dev->gmax, 0xff, sizeof(int32_t), s);  // -1
+  if (n <= 0) return 0;
+  int grid = div_up(n, kNT);
+  if (grid > 1184) grid = 1184;
+  k_gmax<<<grid, kNT, 0, s>>>(colors, n, dev);
+  return 1;
+}
+
+int launch_fill(int32_t *p, size_t n, int32_t v, cudaStream_t s) {
+  if (n == 0) return 0;
+  long long grid = div_up((long long)n, kNT);
+  if (grid > 4096) grid = 4096;
+  k_fill<<<(int)grid, kNT, 0, s>>>(p, n, v);
+  return 1;
+}
+
+}  // namespace bgpc

@@ -1,0 +1,190 @@
+// Internal declarations of the GB300 BGPC/D2GC library (not part of the ABI).
+//
+// Device data layout (all int32 unless noted; sizes for the power-law 4M x 4M
+// graph in brackets):
+//   graph (caller)  a_ptr[n_a+1] a_idx[nnz] b_ptr[n_b+1] b_idx[nnz]    [~0.55 GB]
+//   tpos[nnz]       CSR entry -> CSC position of the same edge (static)
+//   nc[nnz]         net-major color mirror: nc[f] for CSC entry f of net v is
+//                   the published color of b_idx[f], or -2 - pos if b_idx[f]
+//                   is in the current work queue W at position pos and not yet
+//                   published.  The two-hop gather of Alg. 4 streams nc
+//                   contiguously per net instead of gathering c[b_idx[f]].
+//   npos[nnz]       net-major W position (-1 when not in W), for detection
+//   nown[nnz] (u8)  1 if b_idx[f] owns net v (largest net, ties larger id)
+//   s_own, d2tot [n_a]   |vtxs(own(w))| and sum over nets(w) of |vtxs(v)|
+//   W0/W1, kofs, stage, newpos [n_a], lose [n_a] (u8)
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "../../include/bgpc.h"
+
+namespace bgpc {
+
+// ---------------------------------------------------------------- errors
+enum : int32_t {
+  ERR_RANGE = 1,      // index out of range / bad pointer array
+  ERR_UNSORTED = 2,   // adjacency not sorted or has duplicates
+  ERR_MISMATCH = 4,   // CSR and CSC disagree
+  ERR_RANK = 8,       // rank is not a permutation
+  ERR_INTERNAL = 16,  // a device consistency check failed
+  ERR_COLOR = 32,     // a color outside the bound the kernels were sized for
+};
+
+constexpr int kMaxChunk = 64;       // C <= 64: adjacency masks are 64-bit
+constexpr int kSmallWindow = 512;   // bits of the per-vertex small-path window
+constexpr int kSmallD2 = 448;       // small path: sum of net sizes <= this
+constexpr int kPairCap = 1024;      // small path: (vertex, net) pairs per chunk
+constexpr int kDetectWarpMax = 32;  // nets up to this size use the warp tier
+
+// Device scalars shared by the kernels of one call.
+struct DevScalars {
+  int32_t err;
+  int32_t gmax;      // largest color currently in c
+  int32_t m_next;    // |W_{r+1}|
+  int32_t nbig_t;    // nets with |vtxs| > T
+  int32_t nbig_d;    // nets with |vtxs| > kDetectWarpMax
+  int32_t maxnet;    // largest net
+  int32_t maxcolor;  // for validation / statistics
+  int32_t pad;
+  unsigned long long trav;   // traversed two-hop entries of the round
+  unsigned long long incid;  // incidences sum over W_r of |nets(w)| of the round
+  unsigned long long acc[4]; // reductions (statistics)
+};
+
+template <typename T>
+struct Buf {
+  T *p = nullptr;
+  size_t cap = 0;
+};
+
+}  // namespace bgpc
+
+struct bgpc_ctx {
+  int device = 0;
+  int num_sms = 0;
+  int smem_optin = 0;  // max dynamic shared memory per block (bytes)
+  bgpc::Buf<int32_t> tpos, nc, npos;
+  bgpc::Buf<uint8_t> nown;
+  bgpc::Buf<int32_t> s_own, d2tot, W0, W1, kofs, stage, newpos;
+  bgpc::Buf<uint8_t> lose;
+  bgpc::Buf<int32_t> blocksum, bigt, bigd;
+  bgpc::Buf<int32_t> wlist;            // chunks of the round ordered by wave
+  int32_t *h_wlist = nullptr;          // pinned host staging of wlist
+  size_t h_wlist_cap = 0;
+  bgpc::Buf<int32_t> cptr, cidx;       // D2GC closed neighbourhoods
+  bgpc::Buf<int32_t> dtab;             // per-slot color tables (detection)
+  bgpc::Buf<int32_t> vtab;             // per-slot color counts (validation)
+  size_t dtab_filled = 0;              // entries of dtab already set to INT_MAX
+  bgpc::Buf<unsigned long long> card;  // color-set cardinalities
+  bgpc::Buf<uint8_t> bad;              // validation flags
+  bgpc::DevScalars *dev = nullptr;     // device scalars
+  std::vector<cudaEvent_t> events;     // phase timing (opts.profile)
+  bgpc::DevScalars *host = nullptr;    // pinned mirror
+};
+
+namespace bgpc {
+
+// Grow a device buffer to at least n elements (contents not preserved).
+template <typename T>
+inline cudaError_t grow(Buf<T> &b, size_t n) {
+  if (n <= b.cap) return cudaSuccess;
+  if (b.p) cudaFree(b.p);
+  b.p = nullptr;
+  b.cap = 0;
+  size_t want = n + n / 8 + 64;
+  cudaError_t e = cudaMalloc((void **)&b.p, want * sizeof(T));
+  if (e != cudaSuccess) return e;
+  b.cap = want;
+  return cudaSuccess;
+}
+
+template <typename T>
+inline void release(Buf<T> &b) {
+  if (b.p) cudaFree(b.p);
+  b.p = nullptr;
+  b.cap = 0;
+}
+
+inline int div_up(long long a, long long b) { return (int)((a + b - 1) / b); }
+
+// ------------------------------------------------------------ launchers
+// Setup (bgpc_setup.cu)
+int launch_check_ptr(const int32_t *ptr, int32_t n, int32_t nnz, int32_t *err, cudaStream_t s);
+int launch_check_rows(const int32_t *ptr, const int32_t *idx, int32_t n, int32_t bound,
+                       int32_t *err, int sms, cudaStream_t s);
+int launch_tpos(const bgpc_graph_t &g, int32_t *tpos, int32_t *err, int sms, cudaStream_t s);
+int launch_vertex_static(const bgpc_graph_t &g, const int32_t *tpos, int32_t *s_own,
+                          int32_t *d2tot, uint8_t *nown, int sms, cudaStream_t s);
+int launch_net_static(const bgpc_graph_t &g, int32_t T, int32_t *bigt, int32_t *bigd,
+                       DevScalars *dev, cudaStream_t s);
+int launch_init_queue(const int32_t *rank, int32_t n_a, int32_t *W, int32_t *err, cudaStream_t s);
+int launch_init_mirror(const bgpc_graph_t &g, const int32_t *rank, const int32_t *tpos,
+                        int32_t *nc, int32_t *npos, int32_t *colors, int sms, cudaStream_t s);
+int launch_closed_nbhd(const bgpc_ugraph_t &g, int32_t *cptr, int32_t *cidx, int sms,
+                        cudaStream_t s);
+
+// Coloring (bgpc_color.cu)
+struct WaveArgs {
+  const int32_t *a_ptr, *a_idx, *b_ptr;
+  const int32_t *nc;
+  const int32_t *W;
+  const int32_t *kofs;
+  const int32_t *s_own;
+  const int32_t *d2tot;
+  int32_t *stage;
+  const DevScalars *dev;
+  int32_t *err;
+  int32_t m, C, T;
+  const int32_t *chunks;       // chunk indices of this wave
+  int32_t nchunks;
+  int32_t maxnet;
+  int32_t cbw;                 // bytemap capacity in bytes (multiple of 16)
+};
+// Returns the dynamic shared memory the wave kernel needs for capacity cbw.
+size_t wave_smem_bytes(int32_t cbw);
+// Largest byte-map capacity the wave kernel can hold in shared memory.
+int32_t wave_max_cbw(int smem_optin);
+cudaError_t launch_color_wave(int policy, const WaveArgs &a, int sms, int smem_optin,
+                              cudaStream_t s);
+int launch_publish(const int32_t *a_ptr, const int32_t *tpos, const int32_t *W,
+                   const int32_t *stage, const int32_t *chunks, int32_t nchunks, int32_t C,
+                   int32_t m, int32_t *nc, int32_t *colors, DevScalars *dev, int sms,
+                   cudaStream_t s);
+
+// Wave of chunk j under Q waves: the Weyl sequence frac(j * phi), phi =
+// 0x9E3779B9 / 2^32, scaled to [0, Q).
+inline int32_t wave_of(int64_t j, int32_t Q) {
+  uint32_t x = (uint32_t)((uint64_t)j * 0x9E3779B9ull);
+  return (int32_t)(((uint64_t)x * (uint64_t)Q) >> 32);
+}
+
+// Detection, compaction, per-round bookkeeping (bgpc_detect.cu)
+int launch_kofs(const int32_t *b_ptr, const int32_t *nc_unused, const int32_t *npos,
+                 const uint8_t *nown, const int32_t *bigt, int32_t nbig, int32_t *kofs,
+                 int sms, cudaStream_t s);
+int launch_trav(const int32_t *a_ptr, const int32_t *W, const int32_t *d2tot, int32_t m,
+                 DevScalars *dev, cudaStream_t s);
+int launch_detect(const int32_t *b_ptr, int32_t n_b, const int32_t *nc, const int32_t *npos,
+                   const int32_t *bigd, int32_t nbigd, int32_t *dtab, int32_t tabcap,
+                   int32_t nslots, uint8_t *lose, int sms, cudaStream_t s);
+int launch_compact(const uint8_t *lose, const int32_t *W, int32_t m, int32_t *newpos,
+                    int32_t *Wn, int32_t *blocksum, DevScalars *dev, cudaStream_t s);
+int launch_relabel(const int32_t *a_ptr, const int32_t *tpos, const int32_t *W, int32_t m,
+                    uint8_t *lose, const int32_t *newpos, int32_t *nc, int32_t *npos,
+                    int32_t *colors, int sms, cudaStream_t s);
+int launch_gmax(const int32_t *colors, int32_t n, DevScalars *dev, cudaStream_t s);
+int launch_fill(int32_t *p, size_t n, int32_t v, cudaStream_t s);
+
+// Statistics and validation (bgpc_metrics.cu)
+int launch_card(const int32_t *colors, int32_t n, unsigned long long *card, int32_t ncard,
+                 int32_t *err, cudaStream_t s);
+int launch_card_stats(const unsigned long long *card, int32_t ncard, DevScalars *dev,
+                       cudaStream_t s);
+int launch_validate(const bgpc_graph_t &g, const int32_t *colors, const int32_t *bigd,
+                     int32_t nbigd, int32_t *tab, int32_t tabcap, int32_t nslots,
+                     uint8_t *bad, DevScalars *dev, int sms, cudaStream_t s);
+
+}  // namespace bgpc

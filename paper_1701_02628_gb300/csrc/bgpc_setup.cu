@@ -1,0 +1,258 @@
+// Setup of one coloring call: input validation, the static per-graph
+// analysis (CSR->CSC edge map, owner nets, two-hop volumes) and the initial
+// work queue and net-major mirrors (Alg. 1, first two lines: W <- V_color,
+// c <- -1).  Also the D2GC front end: closed neighbourhoods N[u] (Sec. IV).
+#include "bgpc_internal.cuh"
+
+namespace bgpc {
+namespace {
+
+constexpr int kNT = 256;
+
+__global__ void k_check_ptr(const int32_t *__restrict__ ptr, int32_t n, int32_t nnz,
+                            int32_t *err) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i > n) return;
+  int32_t x = ptr[i];
+  bool bad = (x < 0 || x > nnz);
+  if (i == 0) bad |= (x != 0);
+  if (i == n) bad |= (x != nnz);
+  if (i < n) bad |= (ptr[i + 1] < x);
+  if (bad) atomicOr(err, ERR_RANGE);
+}
+
+// One warp per row: indices in [0, bound), strictly increasing.
+__global__ void k_check_rows(const int32_t *__restrict__ ptr, const int32_t *__restrict__ idx,
+                             int32_t n, int32_t bound, int32_t *err) {
+  const int lane = threadIdx.x & 31;
+  int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t r = warp; r < n; r += nwarps) {
+    int32_t beg = ptr[r], end = ptr[r + 1];
+    int flags = 0;
+    for (int32_t e = beg + lane; e < end; e += 32) {
+      int32_t x = idx[e];
+      if (x < 0 || x >= bound) flags |= ERR_RANGE;
+      if (e + 1 < end && idx[e + 1] <= x) flags |= ERR_UNSORTED;
+    }
+    if (flags) atomicOr(err, flags);
+  }
+}
+
+// tpos[i] = position of w inside vtxs(a_idx[i]) for CSR entry i of vertex w
+// (binary search in the sorted CSC column); a miss means CSR and CSC differ.
+__global__ void k_tpos(const int32_t *__restrict__ a_ptr, const int32_t *__restrict__ a_idx,
+                       const int32_t *__restrict__ b_ptr, const int32_t *__restrict__ b_idx,
+                       int32_t n_a, int32_t *__restrict__ tpos, int32_t *err) {
+  const int lane = threadIdx.x & 31;
+  int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t w = warp; w < n_a; w += nwarps) {
+    int32_t beg = a_ptr[w], end = a_ptr[w + 1];
+    for (int32_t i = beg + lane; i < end; i += 32) {
+      int32_t v = a_idx[i];
+      int32_t lo = b_ptr[v], hi = b_ptr[v + 1];
+      while (lo < hi) {
+        int32_t mid = lo + ((hi - lo) >> 1);
+        if (b_idx[mid] < (int32_t)w) lo = mid + 1; else hi = mid;
+      }
+      if (lo >= b_ptr[v + 1] || b_idx[lo] != (int32_t)w) {
+        atomicOr(err, ERR_MISMATCH);
+        lo = b_ptr[v];  // keep the map in range
+      }
+      tpos[i] = lo;
+    }
+  }
+}
+
+// Per vertex: owner net (largest, ties -> larger id), its size, the sum of
+// its net sizes (two-hop volume incl. w itself), and the owner flag nown[]
+// of every CSC entry.
+__global__ void k_vertex_static(const int32_t *__restrict__ a_ptr,
+                                const int32_t *__restrict__ a_idx,
+                                const int32_t *__restrict__ b_ptr,
+                                const int32_t *__restrict__ tpos, int32_t n_a,
+                                int32_t *__restrict__ s_own, int32_t *__restrict__ d2tot,
+                                uint8_t *__restrict__ nown) {
+  const int lane = threadIdx.x & 31;
+  int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t w = warp; w < n_a; w += nwarps) {
+    int32_t beg = a_ptr[w], end = a_ptr[w + 1];
+    long long sum = 0;
+    // pack (size, net) so that max() breaks ties towards the larger net id
+    unsigned long long best = 0;
+    for (int32_t i = beg + lane; i < end; i += 32) {
+      int32_t v = a_idx[i];
+      int32_t s = b_ptr[v + 1] - b_ptr[v];
+      sum += s;
+      unsigned long long key = ((unsigned long long)(uint32_t)s << 32) | (uint32_t)v;
+      if (key > best) best = key;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      sum += __shfl_xor_sync(0xffffffffu, sum, o);
+      unsigned long long ob = __shfl_xor_sync(0xffffffffu, best, o);
+      if (ob > best) best = ob;
+    }
+    int32_t own = (end > beg) ? (int32_t)(best & 0xffffffffu) : -1;
+    if (lane == 0) {
+      s_own[w] = (end > beg) ? (int32_t)(best >> 32) : 0;
+      d2tot[w] = (int32_t)sum;
+    }
+    for (int32_t i = beg + lane; i < end; i += 32) nown[tpos[i]] = (a_idx[i] == own) ? 1 : 0;
+  }
+}
+
+// Largest net, and the lists of nets above T (reverse first fit) and above
+// the warp-detection size.  List order does not affect any result.
+__global__ void k_net_static(const int32_t *__restrict__ b_ptr, int32_t n_b, int32_t T,
+                             int32_t *__restrict__ bigt, int32_t *__restrict__ bigd,
+                             DevScalars *dev) {
+  int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int32_t s = 0;
+  if (v < n_b) {
+    s = b_ptr[v + 1] - b_ptr[v];
+    if (s > T) bigt[atomicAdd(&dev->nbig_t, 1)] = (int32_t)v;
+    if (s > kDetectWarpMax) bigd[atomicAdd(&dev->nbig_d, 1)] = (int32_t)v;
+  }
+  for (int o = 16; o > 0; o >>= 1) s = max(s, __shfl_xor_sync(0xffffffffu, s, o));
+  if ((threadIdx.x & 31) == 0 && s > 0) atomicMax(&dev->maxnet, s);
+}
+
+// W_0 = V_A in rank order: W[rank[w]] = w, and a check that rank is a
+// permutation (every slot written exactly once).
+__global__ void k_queue_scatter(const int32_t *__restrict__ rank, int32_t n, int32_t *W,
+                                int32_t *err) {
+  int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (w >= n) return;
+  if (!rank) { W[w] = (int32_t)w; return; }
+  int32_t r = rank[w];
+  if (r < 0 || r >= n) { atomicOr(err, ERR_RANK); return; }
+  W[r] = (int32_t)w;
+}
+
+__global__ void k_queue_check(const int32_t *__restrict__ rank, int32_t n,
+                              const int32_t *__restrict__ W, int32_t *err) {
+  int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n || !rank) return;
+  int32_t w = W[p];
+  if (w < 0 || w >= n || rank[w] != (int32_t)p) atomicOr(err, ERR_RANK);
+}
+
+// Round 1: every vertex is in W at position pos = rank[w] (or w).
+__global__ void k_init_mirror(const int32_t *__restrict__ a_ptr, const int32_t *__restrict__ rank,
+                              const int32_t *__restrict__ tpos, int32_t n_a,
+                              int32_t *__restrict__ nc, int32_t *__restrict__ npos,
+                              int32_t *__restrict__ colors) {
+  const int lane = threadIdx.x & 31;
+  int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t w = warp; w < n_a; w += nwarps) {
+    int32_t pos = rank ? rank[w] : (int32_t)w;
+    int32_t beg = a_ptr[w], end = a_ptr[w + 1];
+    for (int32_t i = beg + lane; i < end; i += 32) {
+      int32_t f = tpos[i];
+      nc[f] = -2 - pos;
+      npos[f] = pos;
+    }
+    if (lane == 0) colors[w] = -1;
+  }
+}
+
+// N[u] = adj(u) with u inserted at its sorted place: cptr[u] = ptr[u] + u.
+__global__ void k_closed_nbhd(const int32_t *__restrict__ ptr, const int32_t *__restrict__ idx,
+                              int32_t n, int32_t *__restrict__ cptr, int32_t *__restrict__ cidx) {
+  const int lane = threadIdx.x & 31;
+  int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t u = warp; u < n; u += nwarps) {
+    int32_t beg = ptr[u], end = ptr[u + 1];
+    int32_t obase = beg + (int32_t)u;
+    if (lane == 0) {
+      cptr[u] = obase;
+      if (u == n - 1) cptr[n] = end + n;
+    }
+    int32_t below = 0;  // neighbours smaller than u seen so far
+    for (int32_t e0 = beg; e0 < end; e0 += 32) {
+      int32_t e = e0 + lane;
+      int32_t x = (e < end) ? idx[e] : INT32_MAX;
+      unsigned lt = __ballot_sync(0xffffffffu, e < end && x < (int32_t)u);
+      if (e < end) {
+        int32_t o = (x < (int32_t)u) ? (e - beg) : (e - beg + 1);
+        cidx[obase + o] = x;
+      }
+      below += __popc(lt);
+    }
+    if (lane == 0) cidx[obase + below] = (int32_t)u;
+  }
+}
+
+inline int grid_warps(long long items, int sms) {
+  long long g = div_up(items * 32, kNT);
+  long long cap = (long long)sms * 16;
+  if (g > cap) g = cap;
+  if (g < 1) g = 1;
+  return (int)g;
+}
+
+}  // namespace
+
+int launch_check_ptr(const int32_t *ptr, int32_t n, int32_t nnz, int32_t *err, cudaStream_t s) {
+  k_check_ptr<<<div_up((long long)n + 1, kNT), kNT, 0, s>>>(ptr, n, nnz, err);
+  return 1;
+}
+
+int launch_check_rows(const int32_t *ptr, const int32_t *idx, int32_t n, int32_t bound,
+                       int32_t *err, int sms, cudaStream_t s) {
+  if (n <= 0) return 0;
+  k_check_rows<<<grid_warps(n, sms), kNT, 0, s>>>(ptr, idx, n, bound, err);
+  return 1;
+}
+
+int launch_tpos(const bgpc_graph_t &g, int32_t *tpos, int32_t *err, int sms, cudaStream_t s) {
+  if (g.n_a <= 0) return 0;
+  k_tpos<<<grid_warps(g.n_a, sms), kNT, 0, s>>>(g.a_ptr, g.a_idx, g.b_ptr, g.b_idx, g.n_a,
+                                                 tpos, err);
+  return 1;
+}
+
+int launch_vertex_static(const bgpc_graph_t &g, const int32_t *tpos, int32_t *s_own,
+                          int32_t *d2tot, uint8_t *nown, int sms, cudaStream_t s) {
+  if (g.n_a <= 0) return 0;
+  k_vertex_static<<<grid_warps(g.n_a, sms), kNT, 0, s>>>(g.a_ptr, g.a_idx, g.b_ptr, tpos,
+                                                          g.n_a, s_own, d2tot, nown);
+  return 1;
+}
+
+int launch_net_static(const bgpc_graph_t &g, int32_t T, int32_t *bigt, int32_t *bigd,
+                       DevScalars *dev, cudaStream_t s) {
+  if (g.n_b <= 0) return 0;
+  k_net_static<<<div_up(g.n_b, kNT), kNT, 0, s>>>(g.b_ptr, g.n_b, T, bigt, bigd, dev);
+  return 1;
+}
+
+int launch_init_queue(const int32_t *rank, int32_t n_a, int32_t *W, int32_t *err,
+                       cudaStream_t s) {
+  if (n_a <= 0) return 0;
+  if (rank) cudaMemsetAsync(W, 0xff, sizeof(int32_t) * (size_t)n_a, s);
+  k_queue_scatter<<<div_up(n_a, kNT), kNT, 0, s>>>(rank, n_a, W, err);
+  if (rank) k_queue_check<<<div_up(n_a, kNT), kNT, 0, s>>>(rank, n_a, W, err);
+  return rank ? 2 : 1;
+}
+
+int launch_init_mirror(const bgpc_graph_t &g, const int32_t *rank, const int32_t *tpos,
+                        int32_t *nc, int32_t *npos, int32_t *colors, int sms, cudaStream_t s) {
+  if (g.n_a <= 0) return 0;
+  k_init_mirror<<<grid_warps(g.n_a, sms), kNT, 0, s>>>(g.a_ptr, rank, tpos, g.n_a, nc, npos,
+                                                        colors);
+  return 1;
+}
+
+int launch_closed_nbhd(const bgpc_ugraph_t &g, int32_t *cptr, int32_t *cidx, int sms,
+                        cudaStream_t s) {
+  if (g.n <= 0) return 0;
+  k_closed_nbhd<<<grid_warps(g.n, sms), kNT, 0, s>>>(g.ptr, g.idx, g.n, cptr, cidx);
+  return 1;
+}
+
+}  // namespace bgpc

@@ -7,6 +7,12 @@ see oracle/bgpc_oracle.c, "O-2".
 """
 
 
+def wave_of(j, Q):
+    """Wave of chunk j: floor(frac(j * phi) * Q) in 32-bit fixed point."""
+    x = (j * 0x9E3779B9) % (1 << 32)
+    return (x * Q) >> 32
+
+
 def nbors(nets_of, vtxs_of, w):
     out = set()
     for v in nets_of[w]:
@@ -93,9 +99,8 @@ def rs(n_a, nets, pol=0, C=64, Q=16, T=64, rank=None, max_rounds=10_000):
         m = len(W)
         nch = (m + C - 1) // C
         for q in range(Q):
-            jlo, jhi = q * nch // Q, (q + 1) * nch // Q
             staged = {}
-            for j in range(jlo, jhi):
+            for j in [j for j in range(nch) if wave_of(j, Q) == q]:
                 L = {}
                 st = {"col_max": max(max(S), 0) if S else 0, "col_next": 0}
                 for w in W[j * C:(j + 1) * C]:

@@ -1,0 +1,260 @@
+"""GPU parity: the CUDA path, called through the C ABI, against the CPU
+oracle on the same seeded inputs.  Colors, round counts, |W_r| and the
+traversed two-hop entries per round must match bit for bit."""
+import numpy as np
+import pytest
+import torch
+
+import graphgen as gg
+import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+POLICIES = [O.FF, O.B1, O.B2, O.B2X]
+
+
+@pytest.fixture(scope="module")
+def bg():
+    import paper_1701_02628_gb300 as m
+    from paper_1701_02628_gb300 import build
+    build.build()
+    return m
+
+
+@pytest.fixture(scope="module")
+def ctx(bg):
+    return bg.Context(0)
+
+
+def run_gpu(bg, ctx, g, **kw):
+    dg = bg.DeviceGraph.from_host(g, "cuda:0")
+    rank = kw.pop("rank", None)
+    if rank is not None:
+        kw["rank"] = torch.as_tensor(rank, dtype=torch.int32, device="cuda:0")
+    colors, st, rc = bg.bgpc_color(ctx, dg, **kw)
+    torch.cuda.synchronize()
+    return colors.cpu().numpy(), st, rc, dg
+
+
+def assert_parity(bg, ctx, g, policy=O.FF, chunk=64, waves=16, big_net=64, rank=None):
+    ref = O.rs_color(g, policy, chunk=chunk, waves=waves, big_net=big_net, rank=rank,
+                     nthreads=8)
+    assert ref.status == O.OK
+    got, st, rc, dg = run_gpu(bg, ctx, g, policy=policy, chunk=chunk, waves=waves,
+                              big_net=big_net, rank=rank, validate=True)
+    assert rc == bg.BGPC_OK
+    bad = np.nonzero(got != ref.colors)[0]
+    assert bad.size == 0, f"{bad.size} colors differ, first at {bad[:8]}"
+    assert st["rounds"] == ref.rounds
+    assert st["w_per_round"] == ref.w_per_round.tolist()[:64]
+    assert st["trav_per_round"] == ref.trav_per_round.tolist()[:64]
+    assert st["colors"] == int(ref.colors.max()) + 1
+    assert bg.bgpc_validate(ctx, dg, torch.as_tensor(got, device="cuda:0")) == 0
+    return st
+
+
+# ------------------------------------------------------------------ configs
+
+def test_config1_random_2000(bg, ctx):
+    g = gg.random_bipartite(2000, 2000, 5, seed=1)
+    st = assert_parity(bg, ctx, g)
+    assert st["w_per_round"][0] == 2000
+
+
+@pytest.mark.parametrize("policy", POLICIES)
+def test_policies_random(bg, ctx, policy):
+    g = gg.random_bipartite(5000, 3000, 6, seed=21)
+    assert_parity(bg, ctx, g, policy=policy)
+
+
+@pytest.mark.parametrize("policy", POLICIES)
+def test_policies_stencil(bg, ctx, policy):
+    assert_parity(bg, ctx, gg.stencil9(96), policy=policy)
+
+
+@pytest.mark.parametrize("policy", POLICIES)
+def test_policies_power_law(bg, ctx, policy):
+    """Small Chung-Lu graph: hub nets above T (reverse first fit) and large
+    two-hop volumes (the CTA-wide byte-map path)."""
+    g = gg.chung_lu(20000, 16, 1500, 2.1, seed=4)
+    assert_parity(bg, ctx, g, policy=policy)
+
+
+@pytest.mark.parametrize("chunk,waves,big_net", [(1, 1, O.NO_BIG), (7, 3, 2), (32, 16, 0),
+                                                 (64, 1, 8), (64, 64, O.NO_BIG), (13, 5, 64)])
+def test_semantic_parameters(bg, ctx, chunk, waves, big_net):
+    g = gg.chung_lu(6000, 10, 600, 2.1, seed=8)
+    assert_parity(bg, ctx, g, chunk=chunk, waves=waves, big_net=big_net)
+
+
+@pytest.mark.parametrize("policy", [O.FF, O.B1, O.B2])
+def test_rank_order(bg, ctx, policy):
+    g = gg.random_bipartite(4000, 2500, 7, seed=5)
+    rank = np.random.default_rng(3).permutation(g.n_a).astype(np.int32)
+    assert_parity(bg, ctx, g, policy=policy, rank=rank)
+
+
+@pytest.mark.parametrize("seed", range(24))
+def test_fuzz_small_graphs(bg, ctx, seed):
+    """Sizes 1..5000, skewed degrees, empty nets, isolated vertices, giant nets."""
+    rng = np.random.default_rng(1000 + seed)
+    n_a = int(rng.integers(1, 5000))
+    n_b = int(rng.integers(1, 3000))
+    kind = seed % 4
+    nets = []
+    for v in range(n_b):
+        if kind == 0:
+            s = int(rng.integers(0, 6))
+        elif kind == 1:
+            s = int(min(n_a, rng.pareto(1.2) * 2))
+        elif kind == 2:
+            s = int(rng.integers(0, 3)) if v else n_a  # one giant net
+        else:
+            s = int(rng.integers(0, min(n_a, 40) + 1))
+        nets.append(rng.choice(n_a, size=min(s, n_a), replace=False))
+    g = gg.from_nets(n_a, nets)
+    policy = int(rng.integers(0, 4))
+    chunk = int(rng.choice([1, 5, 32, 64]))
+    waves = int(rng.choice([1, 2, 16]))
+    big_net = int(rng.choice([0, 4, 64, O.NO_BIG]))
+    assert_parity(bg, ctx, g, policy=policy, chunk=chunk, waves=waves, big_net=big_net)
+
+
+# ------------------------------------------------------------------- D2GC
+
+@pytest.mark.parametrize("policy", POLICIES)
+def test_d2gc_rmat_small(bg, ctx, policy):
+    ug = gg.rmat(12, 16, seed=3)
+    ref = O.rs_color(O.closed_nbhd(ug), policy, nthreads=8)
+    dug = bg.DeviceUGraph.from_host(ug, "cuda:0")
+    colors, st, rc = bg.d2gc_color(ctx, dug, policy=policy, validate=True)
+    got = colors.cpu().numpy()
+    assert np.array_equal(got, ref.colors)
+    assert st["rounds"] == ref.rounds
+    assert st["w_per_round"] == ref.w_per_round.tolist()[:64]
+    assert O.d2_conflicts(ug, got) == 0
+
+
+def test_d2gc_closed_forms(bg, ctx):
+    for edges, n, want in [([(i, i + 1) for i in range(9)], 10, None),
+                           ([(0, i) for i in range(1, 7)], 7, list(range(7)))]:
+        ug = gg.from_edges(n, edges)
+        dug = bg.DeviceUGraph.from_host(ug, "cuda:0")
+        colors, st, _ = bg.d2gc_color(ctx, dug, chunk=n, waves=1, big_net=bg.NO_BIG)
+        got = colors.cpu().numpy().tolist()
+        assert got == (want if want is not None else [i % 3 for i in range(n)])
+
+
+# ------------------------------------------------------------- edge cases
+
+def test_empty_and_degenerate(bg, ctx):
+    # no vertices
+    g = gg.from_nets(0, [])
+    got, st, rc, _ = run_gpu(bg, ctx, g)
+    assert rc == 0 and got.size == 0 and st["rounds"] == 0
+    # vertices without nets -> all 0 in one round
+    g = gg.from_nets(100, [[], [], []])
+    got, st, rc, _ = run_gpu(bg, ctx, g)
+    assert got.tolist() == [0] * 100 and st["rounds"] == 1
+    # one vertex
+    g = gg.from_nets(1, [[0]])
+    got, st, rc, _ = run_gpu(bg, ctx, g)
+    assert got.tolist() == [0]
+
+
+def test_giant_clique_net(bg, ctx):
+    """One net holding every vertex forces n distinct colors; with T below its
+    size every vertex takes the reverse first-fit color in round 1."""
+    n = 3000
+    g = gg.from_nets(n, [list(range(n))])
+    st = assert_parity(bg, ctx, g)
+    assert st["rounds"] == 1 and st["colors"] == n
+    st = assert_parity(bg, ctx, g, big_net=O.NO_BIG, chunk=64, waves=4)
+
+
+def test_errors(bg, ctx):
+    g = gg.random_bipartite(300, 200, 4, seed=2)
+    dg = bg.DeviceGraph.from_host(g, "cuda:0")
+    with pytest.raises(bg.BgpcError) as e:
+        bg.bgpc_color(ctx, dg, chunk=65)
+    assert e.value.status == bg.BGPC_EINVAL
+    with pytest.raises(bg.BgpcError) as e:
+        bg.bgpc_color(ctx, dg, waves=0)
+    assert e.value.status == bg.BGPC_EINVAL
+    bad_rank = torch.zeros(g.n_a, dtype=torch.int32, device="cuda:0")
+    with pytest.raises(bg.BgpcError) as e:
+        bg.bgpc_color(ctx, dg, rank=bad_rank, validate=True)
+    assert e.value.status == bg.BGPC_EINVAL
+    # unsorted adjacency
+    a_idx = dg.a_idx.clone()
+    a_idx[0], a_idx[1] = dg.a_idx[1].item(), dg.a_idx[0].item()
+    bad = bg.DeviceGraph(dg.n_a, dg.n_b, dg.a_ptr, a_idx, dg.b_ptr, dg.b_idx)
+    with pytest.raises(bg.BgpcError) as e:
+        bg.bgpc_color(ctx, bad, validate=True)
+    assert e.value.status == bg.BGPC_EUNSORTED
+    # CSR and CSC disagree (an entry moved to another net)
+    a_idx = dg.a_idx.clone()
+    row = g.a_idx[g.a_ptr[0]:g.a_ptr[1]]
+    free = [v for v in range(g.n_b) if v not in set(row.tolist()) and v > row[-1]]
+    a_idx[g.a_ptr[1] - 1] = free[0]
+    bad = bg.DeviceGraph(dg.n_a, dg.n_b, dg.a_ptr, a_idx, dg.b_ptr, dg.b_idx)
+    with pytest.raises(bg.BgpcError) as e:
+        bg.bgpc_color(ctx, bad, validate=True)
+    assert e.value.status == bg.BGPC_EUNSORTED
+    # index out of range
+    a_idx = dg.a_idx.clone()
+    a_idx[g.a_ptr[1] - 1] = g.n_b + 5
+    bad = bg.DeviceGraph(dg.n_a, dg.n_b, dg.a_ptr, a_idx, dg.b_ptr, dg.b_idx)
+    with pytest.raises(bg.BgpcError) as e:
+        bg.bgpc_color(ctx, bad, validate=True)
+    assert e.value.status == bg.BGPC_EINVAL
+    # round cap: a clique under the Jacobi reading needs s rounds
+    clique = bg.DeviceGraph.from_host(gg.from_nets(40, [list(range(40))]), "cuda:0")
+    with pytest.raises(bg.BgpcError) as e:
+        bg.bgpc_color(ctx, clique, chunk=1, waves=1, big_net=bg.NO_BIG, max_rounds=5)
+    assert e.value.status == bg.BGPC_EROUNDS
+    # the context stays usable after errors
+    assert_parity(bg, ctx, g)
+
+
+def test_color_sets(bg, ctx):
+    g = gg.random_bipartite(3000, 2000, 5, seed=9)
+    for pol in POLICIES:
+        got, st, _, _ = run_gpu(bg, ctx, g, policy=pol, want_balance=True)
+        ref = O.balance(got)
+        assert st["n_sets"] == ref["colors"] and st["max_card"] == ref["max_card"]
+        assert abs(st["mean_card"] - ref["mean_card"]) < 1e-9
+        assert abs(st["std_card"] - ref["std_card"]) < 1e-9 * max(1.0, ref["std_card"])
+        card, s2 = bg.bgpc_color_sets(ctx, torch.as_tensor(got, device="cuda:0"), st["colors"])
+        K, rc = O.color_sets(got)
+        assert np.array_equal(card.cpu().numpy(), rc)
+
+
+def test_validate_counts_conflicts(bg, ctx):
+    g = gg.chung_lu(5000, 12, 800, 2.1, seed=6)
+    got, st, _, dg = run_gpu(bg, ctx, g)
+    bad = got.copy()
+    rng = np.random.default_rng(0)
+    bad[rng.choice(g.n_a, 50, replace=False)] = 0
+    bad[:3] = -1
+    assert bg.bgpc_validate(ctx, dg, torch.as_tensor(bad, device="cuda:0")) == O.conflicts(g, bad)
+
+
+# ------------------------------------------------------ wave-by-wave state
+
+def test_wave_snapshots_match(bg, ctx):
+    """The state at the start of every wave (colors and work queue) equals
+    the oracle's, on a graph with several rounds."""
+    g = gg.chung_lu(12000, 16, 1200, 2.1, seed=12)
+    C, Q, T = 32, 4, 16
+    full = O.rs_color(g, O.B2, chunk=C, waves=Q, big_net=T)
+    dg = bg.DeviceGraph.from_host(g, "cuda:0")
+    W_out = torch.empty(g.n_a, dtype=torch.int32, device="cuda:0")
+    for wv in range(1, full.rounds * Q):
+        ref = O.rs_color(g, O.B2, chunk=C, waves=Q, big_net=T, stop_after_waves=wv)
+        colors, st, rc = bg.bgpc_color(ctx, dg, policy=O.B2, chunk=C, waves=Q, big_net=T,
+                                       stop_after_waves=wv, W_out=W_out)
+        assert rc == bg.BGPC_STOPPED and ref.status == O.STOPPED
+        assert st["stopped_m"] == ref.m and st["stopped_wave"] == ref.wave
+        assert np.array_equal(colors.cpu().numpy(), ref.colors)
+        assert np.array_equal(W_out[:ref.m].cpu().numpy(), ref.W)

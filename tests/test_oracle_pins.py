@@ -295,7 +295,7 @@ def test_wave_stepping_reproduces_full_run():
         nxt = O.rs_color(g, pol, chunk=C, waves=Q, big_net=T, stop_after_waves=wv + 1)
         nch = (st.m + C - 1) // C
         q = st.wave
-        chunks = list(range(q * nch // Q, (q + 1) * nch // Q))
+        chunks = [j for j in range(nch) if rs_py.wave_of(j, Q) == q]
         out = O.rs_chunks(g, st.colors, st.W, chunks, pol, chunk=C, big_net=T)
         pos = [p for j in chunks for p in range(j * C, min(st.m, (j + 1) * C))]
         if nxt.status == O.STOPPED and nxt.wave == q + 1:
@@ -303,7 +303,7 @@ def test_wave_stepping_reproduces_full_run():
     # conflict rule on the last round's colors
     st = O.rs_color(g, pol, chunk=C, waves=Q, big_net=T, stop_after_waves=Q - 1)
     nch = (st.m + C - 1) // C
-    chunks = list(range((Q - 1) * nch // Q, nch))
+    chunks = [j for j in range(nch) if rs_py.wave_of(j, Q) == Q - 1]
     out = O.rs_chunks(g, st.colors, st.W, chunks, pol, chunk=C, big_net=T)
     c = st.colors.copy()
     for j in chunks:
