@@ -267,16 +267,28 @@ def run_gpu(args):
     value = world * entries_step * args.steps / (ms_max / 1000.0)
     launches = sum(st["kernel_launches"] for sts in all_stats for st in sts)
 
-    # roofline of the dominant kernel (wave coloring): algorithmic bytes per
-    # launch / mean launch duration, both from the timed region
-    col_ms = sum(st["ms_color"] for sts in all_stats for st in sts)
-    col_n = sum(st["color_launches"] for sts in all_stats for st in sts)
-    col_bytes = sum(4 * (st["trav_total"] + st["incid_total"]) + 12 * st["incid_total"]
-                    + 28 * st["w_total"] for sts in all_stats for st in sts)
+    # roofline of the dominant kernel: algorithmic bytes per launch / mean
+    # launch duration, both over the timed region.  The gather kernel streams
+    # the mirror entries of the vertices that take the multi-CTA path, the
+    # resolve kernel those of the small vertices (4 B per streamed entry, 12 B
+    # per incidence for a_idx and the b_ptr pair, 28 B per small vertex).
+    def tot(key):
+        return sum(st[key] for sts in all_stats for st in sts)
+    n_launch = tot("color_launches")
+    kern = {
+        "k_gather": (tot("ms_gather"),
+                     4 * (tot("trav_large") + tot("incid_large")) + 12 * tot("incid_large")),
+        "k_color_wave": (tot("ms_color"),
+                         4 * (tot("trav_total") - tot("trav_large") + tot("incid_total")
+                              - tot("incid_large")) + 12 * (tot("incid_total") - tot("incid_large"))
+                         + 28 * (tot("w_total") - tot("w_large"))),
+    }
+    dom = max(kern, key=lambda k: kern[k][0])
+    dom_ms, dom_bytes = kern[dom]
     peak, peak_kind = peaks()
-    achieved = (col_bytes / col_n) / (col_ms / col_n / 1000.0) / 1e9 if col_ms > 0 else 0.0
-    phase_ms = {k: sum(st[k] for sts in all_stats for st in sts) / args.steps
-                for k in ("ms_setup", "ms_color", "ms_publish", "ms_detect")}
+    achieved = dom_bytes / (dom_ms / 1000.0) / 1e9 if dom_ms > 0 else 0.0
+    phase_ms = {k: tot(k) / args.steps
+                for k in ("ms_setup", "ms_gather", "ms_color", "ms_publish", "ms_detect")}
 
     # end to end through the public API: H2D of the graph from pinned host
     # memory, coloring, D2H of the colors, every step
@@ -325,7 +337,8 @@ def run_gpu(args):
             per_graph.append({"graph": g.name, "n_a": g.n_a, "nnz": g.nnz, "E2": e2_of(g),
                               "rounds": st["rounds"], "colors": st["colors"],
                               "w_per_round": st["w_per_round"][:12],
-                              "trav_total": st["trav_total"]})
+                              "trav_total": st["trav_total"],
+                              "trav_large": st["trav_large"], "pieces": st["pieces_total"]})
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
@@ -334,12 +347,16 @@ def run_gpu(args):
             "config": {"workload": WORKLOAD, "l2": "inputs larger than L2 (no flush)",
                        "parallelism": "replicas" if world > 1 else "single GPU",
                        "graphs": per_graph, "phase_ms_per_step": phase_ms},
-            "roofline": {"bound": "hbm", "kernel": "k_color_wave",
+            "roofline": {"bound": "hbm", "kernel": dom,
                          "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "peak_kind": peak_kind,
                          "traffic": None,
-                         "bytes_per_launch": col_bytes / max(col_n, 1),
-                         "ms_per_launch": col_ms / max(col_n, 1)},
+                         "bytes_per_launch": dom_bytes / max(n_launch, 1),
+                         "ms_per_launch": dom_ms / max(n_launch, 1),
+                         "launches": n_launch,
+                         "other": {k: {"ms_per_step": v[0] / args.steps,
+                                       "GB_s": (v[1] / (v[0] / 1000.0) / 1e9) if v[0] else 0.0}
+                                   for k, v in kern.items()}},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": launches,

@@ -113,9 +113,12 @@ typedef struct {
     double mean_card, std_card;           /* over non-empty sets (want_balance) */
     int64_t incid_total;                  /* all rounds: sum over W_r of |nets(w)| */
     int64_t w_total;                      /* all rounds: sum of |W_r| */
+    int64_t trav_large, incid_large, w_large; /* the same three over the vertices taking
+                                                 the multi-CTA gather path */
+    int64_t pieces_total;                 /* gather work items, all rounds */
     int64_t kernel_launches;              /* kernels this call launched */
     int64_t color_launches;               /* wave-coloring kernel launches */
-    double ms_setup, ms_color, ms_publish, ms_detect; /* device time per phase (profile) */
+    double ms_setup, ms_color, ms_publish, ms_detect, ms_gather; /* device time per phase (profile) */
 } bgpc_stats_t;
 
 /* Fill `opts` with the defaults: FF, C=64, Q=16, T=64, id order,

@@ -58,9 +58,12 @@ class bgpc_stats_t(ctypes.Structure):
                 ("n_sets", ctypes.c_int32), ("max_card", ctypes.c_int32),
                 ("mean_card", ctypes.c_double), ("std_card", ctypes.c_double),
                 ("incid_total", ctypes.c_int64), ("w_total", ctypes.c_int64),
+                ("trav_large", ctypes.c_int64), ("incid_large", ctypes.c_int64),
+                ("w_large", ctypes.c_int64), ("pieces_total", ctypes.c_int64),
                 ("kernel_launches", ctypes.c_int64), ("color_launches", ctypes.c_int64),
                 ("ms_setup", ctypes.c_double), ("ms_color", ctypes.c_double),
-                ("ms_publish", ctypes.c_double), ("ms_detect", ctypes.c_double)]
+                ("ms_publish", ctypes.c_double), ("ms_detect", ctypes.c_double),
+                ("ms_gather", ctypes.c_double)]
 
 
 EXPORTS = ["bgpc_opts_default", "bgpc_ctx_create", "bgpc_ctx_destroy", "bgpc_color",
@@ -229,9 +232,11 @@ def stats_dict(st: bgpc_stats_t) -> dict:
                 trav_total=st.trav_total, stopped_m=st.stopped_m, stopped_wave=st.stopped_wave,
                 n_sets=st.n_sets, max_card=st.max_card, mean_card=st.mean_card,
                 std_card=st.std_card, incid_total=st.incid_total, w_total=st.w_total,
+                trav_large=st.trav_large, incid_large=st.incid_large, w_large=st.w_large,
+                pieces_total=st.pieces_total,
                 kernel_launches=st.kernel_launches,
                 color_launches=st.color_launches, ms_setup=st.ms_setup, ms_color=st.ms_color,
-                ms_publish=st.ms_publish, ms_detect=st.ms_detect)
+                ms_publish=st.ms_publish, ms_detect=st.ms_detect, ms_gather=st.ms_gather)
 
 
 def bgpc_color(ctx: Context, g: DeviceGraph, colors: torch.Tensor = None, stream=None, **opts):

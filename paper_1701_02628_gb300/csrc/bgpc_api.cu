@@ -79,14 +79,14 @@ int validate_csr(bgpc_ctx_t *ctx, const int32_t *ptr, const int32_t *idx, int32_
 int32_t round_up16(int64_t x) { return (int32_t)((x + 15) & ~(int64_t)15); }
 
 // Phase timing with CUDA events recorded on the launch stream (opts.profile).
-enum Phase { PH_SETUP = 0, PH_COLOR = 1, PH_PUBLISH = 2, PH_DETECT = 3 };
+enum Phase { PH_SETUP = 0, PH_COLOR = 1, PH_PUBLISH = 2, PH_DETECT = 3, PH_GATHER = 4 };
 struct PhaseTimer {
   bgpc_ctx_t *ctx;
   cudaStream_t s;
   bool on;
   int used = 0;
   std::vector<int> phase;
-  double ms[4] = {0, 0, 0, 0};
+  double ms[5] = {0, 0, 0, 0, 0};
   PhaseTimer(bgpc_ctx_t *c, cudaStream_t st, bool enabled) : ctx(c), s(st), on(enabled) {}
   cudaEvent_t ev(int i) {
     while ((int)ctx->events.size() <= i) {
@@ -163,7 +163,9 @@ int color_impl(bgpc_ctx_t *ctx, const bgpc_graph_t &g, const bgpc_opts_t &o, int
   CU(grow(ctx->stage, (size_t)n_a));
   CU(grow(ctx->newpos, (size_t)n_a));
   CU(grow(ctx->lose, (size_t)n_a));
-  CU(grow(ctx->blocksum, (size_t)div_up(n_a, 4096) + 1));
+  CU(grow(ctx->blocksum, (size_t)div_up((long long)n_a + kMaxChunk, 4096) + 1));
+  CU(grow(ctx->segoff, (size_t)n_a + kMaxChunk + 1));
+  CU(grow(ctx->segmap, (size_t)n_a + (size_t)nnz / kPiece + 16));
   CU(grow(ctx->bigt, (size_t)(n_b > 0 ? n_b : 1)));
   CU(grow(ctx->bigd, (size_t)(n_b > 0 ? n_b : 1)));
 
@@ -186,7 +188,7 @@ int color_impl(bgpc_ctx_t *ctx, const bgpc_graph_t &g, const bgpc_opts_t &o, int
   if (ctx->host->err) return err_to_status(ctx->host->err);
   const int32_t nbig_t = ctx->host->nbig_t, nbig_d = ctx->host->nbig_d;
   const int32_t maxnet = ctx->host->maxnet;
-  const int32_t max_cbw = wave_max_cbw(ctx->smem_optin);
+  const int32_t max_words = wave_max_words(ctx->smem_optin);
 
   int32_t *W = ctx->W0.p, *Wn = ctx->W1.p;
   int32_t m = n_a, gmax = -1, r = 0;
@@ -194,11 +196,15 @@ int color_impl(bgpc_ctx_t *ctx, const bgpc_graph_t &g, const bgpc_opts_t &o, int
   const int32_t C = o.chunk, Q = o.waves;
   while (m > 0) {
     if (r >= o.max_rounds) return BGPC_EROUNDS;
-    // every color of this round is <= max(gmax, maxnet - 1, 0) + C * Q
+    // every color of this round is <= max(gmax, maxnet - 1, 0) + C * Q (each
+    // color is at most one above the largest one its chunk can see)
     const int64_t b0 = (int64_t)(gmax > maxnet - 1 ? gmax : maxnet - 1);
-    const int64_t cbw64 = (b0 > 0 ? b0 : 0) + (int64_t)C * Q + C + 2;
-    if (cbw64 > max_cbw) return BGPC_ENOMEM;
-    const int32_t cbw = round_up16(cbw64);
+    const int64_t ncol64 = (b0 > 0 ? b0 : 0) + (int64_t)C * Q + C + 2;
+    const int64_t words64 = ((ncol64 + 31) / 32 + 3) & ~(int64_t)3;
+    if (words64 > max_words) return BGPC_ENOMEM;
+    const int32_t words = (int32_t)words64;
+    const int32_t cbw = words * 32;  // color capacity of bitmaps and tables
+    const int32_t small_ok = (o.policy == BGPC_FF || cbw <= kSmallWindow) ? 1 : 0;
     const int32_t nslots = nbig_d < 2 * sms ? (nbig_d > 0 ? nbig_d : 1) : 2 * sms;
     if ((rc = ensure_table(ctx, (size_t)nslots * (size_t)cbw, s, &nk))) return rc;
 
@@ -206,8 +212,8 @@ int color_impl(bgpc_ctx_t *ctx, const bgpc_graph_t &g, const bgpc_opts_t &o, int
     if (nbig_t > 0)
       nk += launch_kofs(g.b_ptr, ctx->nc.p, ctx->npos.p, ctx->nown.p, ctx->bigt.p, nbig_t,
                         ctx->kofs.p, sms, s);
-    CU(cudaMemsetAsync(&ctx->dev->trav, 0, 2 * sizeof(unsigned long long), s));
-    nk += launch_trav(g.a_ptr, W, ctx->d2tot.p, m, ctx->dev, s);
+    CU(cudaMemsetAsync(&ctx->dev->trav, 0, 5 * sizeof(unsigned long long), s));
+    nk += launch_trav(g.a_ptr, W, ctx->d2tot.p, m, small_ok, ctx->dev, s);
     tm.end(ev, PH_DETECT);
 
     // chunks of every wave (a pure function of nch and Q), uploaded once per round
@@ -229,6 +235,24 @@ int color_impl(bgpc_ctx_t *ctx, const bgpc_graph_t &g, const bgpc_opts_t &o, int
       CU(cudaMemcpyAsync(ctx->wlist.p, ctx->h_wlist, sizeof(int32_t) * (size_t)nch,
                          cudaMemcpyHostToDevice, s));
     }
+    // per-slot forbidden bitmaps of the large vertices of one wave (zero at rest)
+    int64_t maxwave = 0;
+    for (int32_t q = 0; q < Q; q++)
+      maxwave = woff[q + 1] - woff[q] > maxwave ? woff[q + 1] - woff[q] : maxwave;
+    {
+      const size_t gw = (size_t)maxwave * C * (size_t)words;
+      if (gw > ctx->gbm.cap || gw > ctx->gbm_zeroed || (size_t)maxwave * C > ctx->gadj.cap) {
+        CU(grow(ctx->gbm, gw));
+        CU(grow(ctx->gadj, (size_t)maxwave * C));
+        CU(cudaMemsetAsync(ctx->gbm.p, 0, ctx->gbm.cap * sizeof(uint32_t), s));
+        CU(cudaMemsetAsync(ctx->gadj.p, 0, ctx->gadj.cap * sizeof(unsigned long long), s));
+        ctx->gbm_zeroed = ctx->gbm.cap;
+      }
+    }
+    ev = tm.begin();
+    nk += launch_pieces(g.a_ptr, ctx->d2tot.p, W, ctx->wlist.p, (int32_t)nch, C, m, small_ok,
+                        ctx->segoff.p, ctx->blocksum.p, ctx->segmap.p, ctx->dev, s);
+    tm.end(ev, PH_DETECT);
     for (int32_t q = 0; q < Q; q++) {
       if (o.stop_after_waves > 0 && waves_done == o.stop_after_waves) {
         if (o.W_out) CU(cudaMemcpyAsync(o.W_out, W, sizeof(int32_t) * (size_t)m,
@@ -245,6 +269,26 @@ int color_impl(bgpc_ctx_t *ctx, const bgpc_graph_t &g, const bgpc_opts_t &o, int
       const int32_t *wchunks = ctx->wlist.p + woff[q];
       const int32_t nwave = (int32_t)(woff[q + 1] - woff[q]);
       if (nwave > 0) {
+        GatherArgs ga;
+        ga.a_ptr = g.a_ptr;
+        ga.a_idx = g.a_idx;
+        ga.b_ptr = g.b_ptr;
+        ga.nc = ctx->nc.p;
+        ga.W = W;
+        ga.wlist = ctx->wlist.p;
+        ga.segmap = ctx->segmap.p;
+        ga.segoff = ctx->segoff.p;
+        ga.m = m;
+        ga.C = C;
+        ga.slot_lo = (int32_t)(woff[q] * C);
+        ga.slot_hi = (int32_t)(woff[q + 1] * C);
+        ga.words = words;
+        ga.gbm = ctx->gbm.p;
+        ga.gadj = ctx->gadj.p;
+        ev = tm.begin();
+        CU(launch_gather(ga, sms, s));
+        tm.end(ev, PH_GATHER);
+        nk++;
         WaveArgs a;
         a.a_ptr = g.a_ptr;
         a.a_idx = g.a_idx;
@@ -263,9 +307,12 @@ int color_impl(bgpc_ctx_t *ctx, const bgpc_graph_t &g, const bgpc_opts_t &o, int
         a.chunks = wchunks;
         a.nchunks = nwave;
         a.maxnet = maxnet;
-        a.cbw = cbw;
+        a.words = words;
+        a.small_ok = small_ok;
+        a.gbm = ctx->gbm.p;
+        a.gadj = ctx->gadj.p;
         ev = tm.begin();
-        CU(launch_color_wave(o.policy, a, sms, ctx->smem_optin, s));
+        CU(launch_color_wave(o.policy, a, sms, s));
         tm.end(ev, PH_COLOR);
         nk++;
         st.color_launches++;
@@ -288,13 +335,20 @@ int color_impl(bgpc_ctx_t *ctx, const bgpc_graph_t &g, const bgpc_opts_t &o, int
     CU(cudaGetLastError());
     if ((rc = sync_scalars(ctx, s))) return rc;
     tm.collect();
-    if (ctx->host->err) return err_to_status(ctx->host->err);
+    if (ctx->host->err) {
+      ctx->gbm_zeroed = 0;  // a kernel may have stopped before clearing its slots
+      return err_to_status(ctx->host->err);
+    }
     if (r < BGPC_MAX_REPORT) {
       st.w_per_round[r] = m;
       st.trav_per_round[r] = (int64_t)ctx->host->trav;
     }
     st.trav_total += (int64_t)ctx->host->trav;
     st.incid_total += (int64_t)ctx->host->incid;
+    st.trav_large += (int64_t)ctx->host->trav_large;
+    st.incid_large += (int64_t)ctx->host->incid_large;
+    st.w_large += (int64_t)ctx->host->w_large;
+    st.pieces_total += ctx->host->nseg;
     st.w_total += m;
     r++;
     const int32_t mn = ctx->host->m_next;
@@ -326,6 +380,7 @@ int color_impl(bgpc_ctx_t *ctx, const bgpc_graph_t &g, const bgpc_opts_t &o, int
   st.ms_color = tm.ms[PH_COLOR];
   st.ms_publish = tm.ms[PH_PUBLISH];
   st.ms_detect = tm.ms[PH_DETECT];
+  st.ms_gather = tm.ms[PH_GATHER];
   if (stats) *stats = st;
   return BGPC_OK;
 }
@@ -383,7 +438,8 @@ int bgpc_ctx_destroy(bgpc_ctx_t *ctx) {
   release(ctx->kofs); release(ctx->stage); release(ctx->newpos); release(ctx->lose);
   release(ctx->blocksum); release(ctx->bigt); release(ctx->bigd);
   release(ctx->cptr); release(ctx->cidx); release(ctx->dtab); release(ctx->vtab);
-  release(ctx->wlist);
+  release(ctx->wlist); release(ctx->segoff); release(ctx->segmap); release(ctx->gbm);
+  release(ctx->gadj);
   if (ctx->h_wlist) cudaFreeHost(ctx->h_wlist);
   release(ctx->card); release(ctx->bad);
   for (cudaEvent_t e : ctx->events) cudaEventDestroy(e);

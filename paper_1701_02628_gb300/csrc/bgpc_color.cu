@@ -79,26 +79,39 @@ __device__ __forceinline__ int32_t block_excl_scan(int32_t v, int32_t *red, int3
   return before + inc - v;
 }
 
-// ------------------------------------------------ byte-map searches (CTA)
-// bytes[x] != 0 means color x is forbidden.  `lim` is a multiple of 16.
+// ------------------------------------------- bitmap searches (CTA, smem)
+// bm[x >> 5] bit (x & 31) set means color x is forbidden; `words` is a multiple
+// of 4 and every color >= 32 * words is free.  Thread t of a tile covers the
+// 128 colors of one uint4.
 
-// Smallest free x with p <= x < lim, or lim.
+__device__ __forceinline__ uint32_t mask_from(int32_t lo, int32_t p) {
+  // bits of the word starting at color lo that are >= p
+  if (p <= lo) return 0xffffffffu;
+  if (p >= lo + 32) return 0u;
+  return 0xffffffffu << (p - lo);
+}
+
+__device__ __forceinline__ uint32_t mask_upto(int32_t lo, int32_t p) {
+  // bits of the word starting at color lo that are <= p
+  if (p >= lo + 31) return 0xffffffffu;
+  if (p < lo) return 0u;
+  return 0xffffffffu >> (31 - (p - lo));
+}
+
+// Smallest free x >= p, or 32 * words if every color up to there is taken.
 template <int NT>
-__device__ int32_t bytes_first_free_up(const uint8_t *bytes, int32_t p, int32_t lim,
-                                       int32_t *red) {
-  for (int32_t base = p & ~15; base < lim; base += NT * 16) {
-    int32_t x0 = base + (int32_t)threadIdx.x * 16;
+__device__ int32_t bm_first_free_up(const uint32_t *bm, int32_t words, int32_t p, int32_t *red) {
+  const int32_t lim = words * 32;
+  for (int32_t base = (p >> 7) << 7; base < lim; base += NT * 128) {
+    const int32_t x0 = base + (int32_t)threadIdx.x * 128;
     int32_t found = INT32_MAX;
     if (x0 < lim) {
-      uint4 v = *reinterpret_cast<const uint4 *>(bytes + x0);
-      uint32_t wv[4] = {v.x, v.y, v.z, v.w};
+      const uint4 v = *reinterpret_cast<const uint4 *>(bm + (x0 >> 5));
+      const uint32_t wv[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
       for (int q = 0; q < 4; q++) {
-        int32_t lo = x0 + 4 * q;
-        uint32_t z = __vcmpeq4(wv[q], 0u);
-        if (lo + 4 <= p) z = 0;
-        else if (lo < p) z &= ~((1u << (8 * (p - lo))) - 1u);
-        if (z && found == INT32_MAX) found = lo + ((__ffs(z) - 1) >> 3);
+        const uint32_t fr = ~wv[q] & mask_from(x0 + 32 * q, p);
+        if (fr && found == INT32_MAX) found = x0 + 32 * q + __ffs(fr) - 1;
       }
     }
     found = block_min<NT>(found, red);
@@ -109,12 +122,19 @@ __device__ int32_t bytes_first_free_up(const uint8_t *bytes, int32_t p, int32_t 
 
 // Largest free x with 0 <= x <= p, or -1.
 template <int NT>
-__device__ int32_t bytes_last_free_down(const uint8_t *bytes, int32_t p, int32_t *red) {
-  for (int32_t top = p; top >= 0; top -= NT * 16) {
-    int32_t hi = top - 16 * (int32_t)threadIdx.x, lo = max(hi - 15, 0);
+__device__ int32_t bm_last_free_down(const uint32_t *bm, int32_t p, int32_t *red) {
+  for (int32_t top = ((p >> 7) << 7) + 127; top >= 0; top -= NT * 128) {
+    const int32_t x0 = top - 127 - (int32_t)threadIdx.x * 128;  // multiple of 128
     int32_t found = -1;
-    for (int32_t x = hi; x >= lo; x--)
-      if (bytes[x] == 0) { found = x; break; }
+    if (x0 >= 0 && x0 <= p) {
+      const uint4 v = *reinterpret_cast<const uint4 *>(bm + (x0 >> 5));
+      const uint32_t wv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+      for (int q = 3; q >= 0; q--) {
+        const uint32_t fr = ~wv[q] & mask_upto(x0 + 32 * q, p);
+        if (fr && found < 0) found = x0 + 32 * q + 31 - __clz(fr);
+      }
+    }
     found = block_max<NT>(found, red);
     if (found >= 0) return found;
   }
@@ -123,22 +143,35 @@ __device__ int32_t bytes_last_free_down(const uint8_t *bytes, int32_t p, int32_t
 
 // The k-th (0-based) free color counting down from top, or -1.
 template <int NT>
-__device__ int32_t bytes_kth_free_down(const uint8_t *bytes, int32_t top, int32_t k,
-                                       int32_t *red) {
+__device__ int32_t bm_kth_free_down(const uint32_t *bm, int32_t top, int32_t k, int32_t *red) {
   int32_t remaining = k;
-  for (int32_t t0 = top; t0 >= 0; t0 -= NT * 16) {
-    int32_t hi = t0 - 16 * (int32_t)threadIdx.x, lo = max(hi - 15, 0);
+  for (int32_t t0 = ((top >> 7) << 7) + 127; t0 >= 0; t0 -= NT * 128) {
+    const int32_t x0 = t0 - 127 - (int32_t)threadIdx.x * 128;
+    uint32_t fr[4] = {0u, 0u, 0u, 0u};
     int32_t cnt = 0;
-    for (int32_t x = hi; x >= lo; x--) cnt += (bytes[x] == 0);
+    if (x0 >= 0 && x0 <= top) {
+      const uint4 v = *reinterpret_cast<const uint4 *>(bm + (x0 >> 5));
+      const uint32_t wv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+      for (int q = 0; q < 4; q++) {
+        fr[q] = ~wv[q] & mask_upto(x0 + 32 * q, top);
+        cnt += __popc(fr[q]);
+      }
+    }
     int32_t total;
-    int32_t excl = block_excl_scan<NT>(cnt, red, &total);
+    const int32_t excl = block_excl_scan<NT>(cnt, red, &total);
     if (remaining < total) {
       int32_t res = -1;
       if (cnt > 0 && excl <= remaining && remaining < excl + cnt) {
         int32_t r = remaining - excl;
-        for (int32_t x = hi; x >= lo; x--) {
-          if (bytes[x] == 0) {
-            if (r == 0) { res = x; break; }
+        for (int q = 3; q >= 0 && res < 0; q--) {
+          uint32_t f = fr[q];
+          const int32_t c = __popc(f);
+          if (r >= c) { r -= c; continue; }
+          while (true) {
+            const int32_t b = 31 - __clz(f);
+            if (r == 0) { res = x0 + 32 * q + b; break; }
+            f &= ~(1u << b);
             r--;
           }
         }
@@ -213,7 +246,13 @@ __device__ __forceinline__ int32_t win_kth_free_down(uint32_t word, int32_t top,
   return __shfl_sync(kFull, res, __ffs(b) - 1);
 }
 
-// ------------------------------------------------------------------ kernel
+// --------------------------------------------------------- resolve kernel
+
+// Whether vertex (d2, deg) takes the fused small path (must agree with the
+// piece count of k_piece_count).
+__device__ __forceinline__ bool is_small(int32_t d2, int32_t deg, bool small_ok) {
+  return small_ok && d2 <= kSmallD2 && deg <= kSmallMaxDeg;
+}
 
 template <int POLICY, int NT>
 __global__ void __launch_bounds__(NT) k_color_wave(WaveArgs a) {
@@ -229,23 +268,23 @@ __global__ void __launch_bounds__(NT) k_color_wave(WaveArgs a) {
   __shared__ uint8_t s_pvert[kPairCap];
   __shared__ int32_t s_red[NW + 1];
   __shared__ int32_t s_state[4];  // col_max, col_next, npairs
-  extern __shared__ __align__(16) uint8_t s_bytes[];
+  extern __shared__ __align__(16) uint32_t s_big[];  // a.words: one large vertex's F
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int32_t gm = a.dev->gmax;
   const int32_t bound = max(max(gm, a.maxnet - 1), 0) + a.C;  // every color of this wave <= bound
-  const int32_t need = ((bound + 1) + 15) & ~15;
-  if (need > a.cbw) {
+  if (bound >= a.words * 32) {
     if (tid == 0 && blockIdx.x == 0) atomicOr(a.err, ERR_COLOR);
     return;
   }
-  const bool small_ok = (POLICY == BGPC_FF) || (bound < kSmallWindow);
+  const bool small_ok = a.small_ok != 0;
   const int32_t col_max0 = max(gm, 0);
 
   for (int32_t t = (int32_t)blockIdx.x; t < a.nchunks; t += (int32_t)gridDim.x) {
     const int32_t j = a.chunks[t];
     const int32_t p0 = j * a.C;
     const int32_t n = min(a.C, a.m - p0);
+    const int64_t slot0 = (int64_t)t * a.C;  // wave-order slot of the chunk's first vertex
 
     // ---- step 0: per-vertex data
     if (tid < n) {
@@ -264,31 +303,23 @@ __global__ void __launch_bounds__(NT) k_color_wave(WaveArgs a) {
     if (tid == 0) { s_state[0] = col_max0; s_state[1] = 0; }
     __syncthreads();
 
-    // ---- step 1: which vertices take the small path; their pair offsets
+    // ---- step 1: small vertices and their (vertex, net) pair offsets
     if (warp == 0) {
       const int i0 = lane, i1 = lane + 32;
-      bool c0 = small_ok && i0 < n && s_d2[i0] <= kSmallD2;
-      bool c1 = small_ok && i1 < n && s_d2[i1] <= kSmallD2;
-      int32_t d0 = c0 ? s_deg[i0] : 0, d1 = c1 ? s_deg[i1] : 0;
-      int32_t inc0 = warp_incl_scan(d0);
-      int32_t tot0 = __shfl_sync(kFull, inc0, 31);
-      int32_t inc1 = warp_incl_scan(d1) + tot0;
-      bool sm0 = c0 && inc0 <= kPairCap;
-      bool sm1 = c1 && inc1 <= kPairCap;
-      // non-small vertices get zero width in the pair prefix
-      if (!sm0) d0 = 0;
-      if (!sm1) d1 = 0;
-      inc0 = warp_incl_scan(d0);
-      tot0 = __shfl_sync(kFull, inc0, 31);
-      inc1 = warp_incl_scan(d1) + tot0;
+      const bool sm0 = i0 < n && is_small(s_d2[i0], s_deg[i0], small_ok);
+      const bool sm1 = i1 < n && is_small(s_d2[i1], s_deg[i1], small_ok);
+      const int32_t d0 = sm0 ? s_deg[i0] : 0, d1 = sm1 ? s_deg[i1] : 0;
+      const int32_t inc0 = warp_incl_scan(d0);
+      const int32_t tot0 = __shfl_sync(kFull, inc0, 31);
+      const int32_t inc1 = warp_incl_scan(d1) + tot0;
       s_ppi[i0] = inc0;
-      if (i1 < kMaxChunk) s_ppi[i1] = inc1;
-      unsigned lg0 = __ballot_sync(kFull, i0 < n && !sm0);
-      unsigned lg1 = __ballot_sync(kFull, i1 < n && !sm1);
-      unsigned long long large = ((unsigned long long)lg1 << 32) | lg0;
-      unsigned long long m0 = large >> i0;
+      s_ppi[i1] = inc1;
+      const unsigned lg0 = __ballot_sync(kFull, i0 < n && !sm0);
+      const unsigned lg1 = __ballot_sync(kFull, i1 < n && !sm1);
+      const unsigned long long large = ((unsigned long long)lg1 << 32) | lg0;
+      const unsigned long long m0 = large >> i0;
       s_next[i0] = m0 ? min(i0 + __ffsll((long long)m0) - 1, n) : n;
-      unsigned long long m1 = (i1 < 64) ? (large >> i1) : 0ull;
+      const unsigned long long m1 = large >> i1;
       s_next[i1] = m1 ? min(i1 + __ffsll((long long)m1) - 1, n) : n;
       if (lane == 31) s_state[2] = inc1;
     }
@@ -296,20 +327,20 @@ __global__ void __launch_bounds__(NT) k_color_wave(WaveArgs a) {
 
     // ---- step 2: (vertex, net) pairs of the small vertices
     const int32_t P = s_state[2];
-    for (int32_t t = tid; t < P; t += NT) {
-      int32_t lo = 0, hi = n - 1;  // smallest i with s_ppi[i] > t
+    for (int32_t pt = tid; pt < P; pt += NT) {
+      int32_t lo = 0, hi = n - 1;  // smallest i with s_ppi[i] > pt
       while (lo < hi) {
         int32_t mid = (lo + hi) >> 1;
-        if (s_ppi[mid] > t) hi = mid; else lo = mid + 1;
+        if (s_ppi[mid] > pt) hi = mid; else lo = mid + 1;
       }
       const int32_t i = lo;
       const int32_t width = (i == 0) ? s_ppi[0] : s_ppi[i] - s_ppi[i - 1];
-      const int32_t tl = t - (s_ppi[i] - width);
+      const int32_t tl = pt - (s_ppi[i] - width);
       const int32_t v = a.a_idx[s_ab[i] + tl];
       const int32_t bp = a.b_ptr[v];
-      s_pstart[t] = bp;
-      s_poff[t] = a.b_ptr[v + 1] - bp;
-      s_pvert[t] = (uint8_t)i;
+      s_pstart[pt] = bp;
+      s_poff[pt] = a.b_ptr[v + 1] - bp;
+      s_pvert[pt] = (uint8_t)i;
     }
     __syncthreads();
 
@@ -320,16 +351,16 @@ __global__ void __launch_bounds__(NT) k_color_wave(WaveArgs a) {
       int32_t sum = 0;
 #pragma unroll
       for (int q = 0; q < PER; q++) {
-        int32_t t = tid * PER + q;
-        loc[q] = (t < P) ? s_poff[t] : 0;
+        int32_t pt = tid * PER + q;
+        loc[q] = (pt < P) ? s_poff[pt] : 0;
         sum += loc[q];
       }
       int32_t total;
       int32_t ex = block_excl_scan<NT>(sum, s_red, &total);
 #pragma unroll
       for (int q = 0; q < PER; q++) {
-        int32_t t = tid * PER + q;
-        if (t < P) s_poff[t] = ex;
+        int32_t pt = tid * PER + q;
+        if (pt < P) s_poff[pt] = ex;
         ex += loc[q];
       }
       if (tid == 0) s_poff[P] = total;
@@ -422,60 +453,46 @@ __global__ void __launch_bounds__(NT) k_color_wave(WaveArgs a) {
       }
       __syncthreads();
       if (L < n) {
-        // ---- large vertex: CTA-wide gather into the byte map
-        for (int32_t x = tid * 16; x < need; x += NT * 16)
-          *reinterpret_cast<uint4 *>(s_bytes + x) = make_uint4(0u, 0u, 0u, 0u);
-        __syncthreads();
-        const int32_t ab = s_ab[L], deg = s_deg[L];
-        int bad = 0;
-        for (int32_t t = warp; t < deg; t += NW) {
-          const int32_t v = a.a_idx[ab + t];
-          const int32_t beg = a.b_ptr[v], end = a.b_ptr[v + 1];
-          for (int32_t e0 = beg + lane; e0 < end; e0 += 128) {
-            int32_t val[4];
-#pragma unroll
-            for (int q = 0; q < 4; q++) {
-              int32_t e = e0 + 32 * q;
-              val[q] = (e < end) ? a.nc[e] : INT32_MIN;
-            }
-#pragma unroll
-            for (int q = 0; q < 4; q++) {
-              const int32_t x = val[q];
-              if (x == INT32_MIN) continue;
-              if (x >= 0) {
-                if (x < need) s_bytes[x] = 1; else bad = 1;
-              } else {
-                const int32_t rel = (-2 - x) - p0;
-                if (rel >= 0 && rel < L) atomicOr(&s_adj[L], 1ull << rel);
-              }
-            }
-          }
+        // ---- large vertex: its gathered forbidden set (k_gather) into shared
+        // memory, clearing the global copy for the next wave
+        const int64_t slot = slot0 + L;
+        uint4 *gsrc = reinterpret_cast<uint4 *>(a.gbm + slot * a.words);
+        uint4 *sdst = reinterpret_cast<uint4 *>(s_big);
+        for (int32_t x = tid; x < (a.words >> 2); x += NT) {
+          sdst[x] = gsrc[x];
+          gsrc[x] = make_uint4(0u, 0u, 0u, 0u);
         }
-        if (bad) atomicOr(a.err, ERR_COLOR);
+        if (tid == 0) {
+          s_adj[L] = a.gadj[slot];
+          a.gadj[slot] = 0ull;
+        }
         __syncthreads();
-        if (tid < L && ((s_adj[L] >> tid) & 1ull)) s_bytes[s_col[tid]] = 1;
+        if (tid < L && ((s_adj[L] >> tid) & 1ull)) {
+          const int32_t c = s_col[tid];
+          atomicOr(&s_big[c >> 5], 1u << (c & 31));
+        }
         __syncthreads();
         const int32_t col_max = s_state[0], col_next = s_state[1];
         int32_t x = -1;
         const int32_t so = s_sown[L];
-        if (so > a.T) x = bytes_kth_free_down<NT>(s_bytes, so - 1, s_k[L], s_red);
+        if (so > a.T) x = bm_kth_free_down<NT>(s_big, so - 1, s_k[L], s_red);
         if (x < 0) {
           if (POLICY == BGPC_B1) {
             if ((s_w[L] & 1) == 0) {
-              x = bytes_last_free_down<NT>(s_bytes, col_max, s_red);
-              if (x < 0) x = bytes_first_free_up<NT>(s_bytes, col_max + 1, need, s_red);
+              x = bm_last_free_down<NT>(s_big, col_max, s_red);
+              if (x < 0) x = bm_first_free_up<NT>(s_big, a.words, col_max + 1, s_red);
             } else {
-              x = bytes_first_free_up<NT>(s_bytes, 0, need, s_red);
+              x = bm_first_free_up<NT>(s_big, a.words, 0, s_red);
             }
           } else if (POLICY == BGPC_B2 || POLICY == BGPC_B2X) {
-            x = bytes_first_free_up<NT>(s_bytes, col_next, need, s_red);
-            if (x > col_max) x = bytes_first_free_up<NT>(s_bytes, 0, need, s_red);
+            x = bm_first_free_up<NT>(s_big, a.words, col_next, s_red);
+            if (x > col_max) x = bm_first_free_up<NT>(s_big, a.words, 0, s_red);
           } else {
-            x = bytes_first_free_up<NT>(s_bytes, 0, need, s_red);
+            x = bm_first_free_up<NT>(s_big, a.words, 0, s_red);
           }
         }
         if (tid == 0) {
-          if (x < 0 || x >= need) { atomicOr(a.err, ERR_COLOR); x = 0; }
+          if (x < 0 || x > bound) { atomicOr(a.err, ERR_COLOR); x = 0; }
           s_col[L] = x;
           int32_t cm = max(col_max, x);
           s_state[0] = cm;
@@ -488,6 +505,167 @@ __global__ void __launch_bounds__(NT) k_color_wave(WaveArgs a) {
     }
     if (tid < n) a.stage[p0 + tid] = s_col[tid];
     __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------ gather kernel
+// One work item = up to kPiece nets of one large vertex.  The CTA collects
+// the colors of the members of those nets (from the snapshot, via nc) into a
+// shared bitmap and the earlier chunk-mates it meets into a 64-bit mask, then
+// ORs both into the vertex's global slot.  A heavy vertex is spread over many
+// CTAs, so no chunk waits for one SM.
+template <int NT>
+__global__ void __launch_bounds__(NT) k_gather(GatherArgs a) {
+  constexpr int NW = NT / 32;
+  extern __shared__ __align__(16) uint32_t s_bm[];
+  __shared__ unsigned long long s_adj;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int32_t sbeg = a.segoff[a.slot_lo], send = a.segoff[a.slot_hi];
+  const int32_t lim = a.words * 32;
+  for (int32_t sg = sbeg + (int32_t)blockIdx.x; sg < send; sg += (int32_t)gridDim.x) {
+    const int2 sm = a.segmap[sg];
+    const int32_t u = sm.x, piece = sm.y;  // wave-order slot, piece of the vertex
+    const int32_t j = a.wlist[u / a.C];
+    const int32_t p0 = j * a.C;
+    const int32_t p = p0 + u % a.C;
+    const int32_t w = a.W[p];
+    const int32_t ibeg = a.a_ptr[w] + piece * kPiece;
+    const int32_t iend = min(a.a_ptr[w + 1], ibeg + kPiece);
+    const bool whole = (a.segoff[u + 1] - a.segoff[u]) == 1;
+    for (int32_t x = tid; x < a.words; x += NT) s_bm[x] = 0u;
+    if (tid == 0) s_adj = 0ull;
+    __syncthreads();
+    const int32_t rel_hi = p - p0;
+    unsigned long long adj = 0ull;
+    int bad = 0;
+    for (int32_t it = ibeg + warp; it < iend; it += NW) {
+      const int32_t v = a.a_idx[it];
+      const int32_t beg = a.b_ptr[v], end = a.b_ptr[v + 1];
+      for (int32_t e0 = beg + lane; e0 < end; e0 += 128) {
+        int32_t val[4];
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+          const int32_t e = e0 + 32 * q;
+          val[q] = (e < end) ? a.nc[e] : INT32_MIN;
+        }
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+          const int32_t x = val[q];
+          if (x == INT32_MIN) continue;
+          if (x >= 0) {
+            if (x < lim) atomicOr(&s_bm[x >> 5], 1u << (x & 31)); else bad = 1;
+          } else {
+            const int32_t rel = (-2 - x) - p0;
+            if (rel >= 0 && rel < rel_hi) adj |= 1ull << rel;
+          }
+        }
+      }
+    }
+    (void)bad;
+    if (adj) atomicOr(&s_adj, adj);
+    __syncthreads();
+    const int64_t slot = (int64_t)(u - a.slot_lo);
+    uint32_t *g = a.gbm + slot * a.words;
+    if (whole) {
+      for (int32_t x = tid; x < a.words; x += NT) g[x] = s_bm[x];
+      if (tid == 0) a.gadj[slot] = s_adj;
+    } else {
+      for (int32_t x = tid; x < a.words; x += NT) {
+        const uint32_t b = s_bm[x];
+        if (b) atomicOr(&g[x], b);
+      }
+      if (tid == 0 && s_adj) atomicOr(&a.gadj[slot], s_adj);
+    }
+    __syncthreads();
+  }
+}
+
+// --------------------------------------------------- pieces of the round
+// Wave-order slot u = (index of its chunk in the wave-ordered chunk list) * C
+// + offset in the chunk.  Large vertices get ceil(deg / kPiece) pieces (at
+// least one), small ones none.
+constexpr int kScanNT = 1024;
+constexpr int kScanPer = 4;
+constexpr int kScanTile = kScanNT * kScanPer;
+
+__device__ __forceinline__ int32_t pieces_of(const int32_t *a_ptr, const int32_t *d2tot,
+                                             const int32_t *W, const int32_t *wlist, int32_t C,
+                                             int32_t m, bool small_ok, int64_t u) {
+  const int64_t p = (int64_t)wlist[u / C] * C + u % C;
+  if (p >= m) return 0;
+  const int32_t w = W[p];
+  const int32_t deg = a_ptr[w + 1] - a_ptr[w];
+  if (is_small(d2tot[w], deg, small_ok)) return 0;
+  return max(1, (deg + kPiece - 1) / kPiece);
+}
+
+__global__ void __launch_bounds__(kScanNT) k_piece_count(const int32_t *__restrict__ a_ptr,
+                                                         const int32_t *__restrict__ d2tot,
+                                                         const int32_t *__restrict__ W,
+                                                         const int32_t *__restrict__ wlist,
+                                                         int32_t nslots, int32_t C, int32_t m,
+                                                         int32_t small_ok,
+                                                         int32_t *__restrict__ segoff,
+                                                         int32_t *__restrict__ blocksum) {
+  __shared__ int32_t red[kScanNT / 32];
+  const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanPer;
+  int32_t c = 0;
+#pragma unroll
+  for (int q = 0; q < kScanPer; q++) {
+    const int64_t u = base + q;
+    if (u < nslots) {
+      const int32_t k = pieces_of(a_ptr, d2tot, W, wlist, C, m, small_ok != 0, u);
+      segoff[u] = k;
+      c += k;
+    }
+  }
+  int32_t total;
+  block_excl_scan<kScanNT>(c, red, &total);
+  if (threadIdx.x == 0) blocksum[blockIdx.x] = total;
+}
+
+__global__ void __launch_bounds__(kScanNT) k_piece_blocks(int32_t *__restrict__ blocksum,
+                                                          int32_t nblocks, int32_t nslots,
+                                                          int32_t *__restrict__ segoff,
+                                                          DevScalars *dev) {
+  __shared__ int32_t red[kScanNT / 32];
+  int32_t carry = 0;
+  for (int32_t b0 = 0; b0 < nblocks; b0 += kScanNT) {
+    const int32_t b = b0 + (int32_t)threadIdx.x;
+    const int32_t x = (b < nblocks) ? blocksum[b] : 0;
+    int32_t total;
+    const int32_t ex = block_excl_scan<kScanNT>(x, red, &total);
+    if (b < nblocks) blocksum[b] = carry + ex;
+    carry += total;
+  }
+  if (threadIdx.x == 0) {
+    dev->nseg = carry;
+    segoff[nslots] = carry;
+  }
+}
+
+__global__ void __launch_bounds__(kScanNT) k_piece_scatter(int32_t nslots,
+                                                           const int32_t *__restrict__ blocksum,
+                                                           int32_t *__restrict__ segoff,
+                                                           int2 *__restrict__ segmap) {
+  __shared__ int32_t red[kScanNT / 32];
+  const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanPer;
+  int32_t k[kScanPer];
+  int32_t c = 0;
+#pragma unroll
+  for (int q = 0; q < kScanPer; q++) {
+    k[q] = (base + q < nslots) ? segoff[base + q] : 0;
+    c += k[q];
+  }
+  int32_t total;
+  int32_t ex = block_excl_scan<kScanNT>(c, red, &total) + blocksum[blockIdx.x];
+#pragma unroll
+  for (int q = 0; q < kScanPer; q++) {
+    if (base + q < nslots) {
+      segoff[base + q] = ex;
+      for (int32_t r = 0; r < k[q]; r++) segmap[ex + r] = make_int2((int32_t)(base + q), r);
+      ex += k[q];
+    }
   }
 }
 
@@ -517,46 +695,76 @@ __global__ void k_publish(const int32_t *__restrict__ a_ptr, const int32_t *__re
   if (lane == 0 && mx >= 0) atomicMax(&dev->gmax, mx);
 }
 
-template <int POLICY, int NT>
-cudaError_t launch_policy(const WaveArgs &a, int sms, int smem_optin, cudaStream_t s) {
-  auto kern = k_color_wave<POLICY, NT>;
-  size_t smem = (size_t)a.cbw;
+constexpr int kWaveNT = 256;
+constexpr int kGatherNT = 256;
+
+template <int POLICY>
+cudaError_t launch_policy(const WaveArgs &a, int sms, cudaStream_t s) {
+  auto kern = k_color_wave<POLICY, kWaveNT>;
+  const size_t smem = (size_t)a.words * 4;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kWaveNT, smem);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   int grid = per_sm * sms;
   if (grid > a.nchunks) grid = a.nchunks;
-  (void)smem_optin;
-  kern<<<grid, NT, smem, s>>>(a);
+  kern<<<grid, kWaveNT, smem, s>>>(a);
   return cudaGetLastError();
 }
 
 }  // namespace
 
-size_t wave_smem_bytes(int32_t cbw) { return (size_t)cbw; }
-
-int32_t wave_max_cbw(int smem_optin) {
+int32_t wave_max_words(int smem_optin) {
   cudaFuncAttributes fa;
   size_t stat = 0;
-  if (cudaFuncGetAttributes(&fa, k_color_wave<BGPC_FF, 256>) == cudaSuccess) stat = fa.sharedSizeBytes;
-  else cudaGetLastError();
-  long long room = (long long)smem_optin - (long long)stat - 1024;
-  return room > 0 ? (int32_t)(room & ~15LL) : 0;
+  if (cudaFuncGetAttributes(&fa, k_color_wave<BGPC_FF, kWaveNT>) == cudaSuccess)
+    stat = fa.sharedSizeBytes;
+  else
+    cudaGetLastError();
+  long long room = ((long long)smem_optin - (long long)stat - 1024) / 4;
+  return room > 0 ? (int32_t)(room & ~3LL) : 0;
 }
 
-cudaError_t launch_color_wave(int policy, const WaveArgs &a, int sms, int smem_optin,
-                              cudaStream_t s) {
+cudaError_t launch_color_wave(int policy, const WaveArgs &a, int sms, cudaStream_t s) {
   if (a.nchunks <= 0) return cudaSuccess;
   switch (policy) {
-    case BGPC_B1: return launch_policy<BGPC_B1, 256>(a, sms, smem_optin, s);
-    case BGPC_B2: return launch_policy<BGPC_B2, 256>(a, sms, smem_optin, s);
-    case BGPC_B2X: return launch_policy<BGPC_B2X, 256>(a, sms, smem_optin, s);
-    default: return launch_policy<BGPC_FF, 256>(a, sms, smem_optin, s);
+    case BGPC_B1: return launch_policy<BGPC_B1>(a, sms, s);
+    case BGPC_B2: return launch_policy<BGPC_B2>(a, sms, s);
+    case BGPC_B2X: return launch_policy<BGPC_B2X>(a, sms, s);
+    default: return launch_policy<BGPC_FF>(a, sms, s);
   }
+}
+
+cudaError_t launch_gather(const GatherArgs &a, int sms, cudaStream_t s) {
+  if (a.slot_hi <= a.slot_lo) return cudaSuccess;
+  auto kern = k_gather<kGatherNT>;
+  const size_t smem = (size_t)a.words * 4;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kGatherNT, smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  kern<<<per_sm * sms, kGatherNT, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+int launch_pieces(const int32_t *a_ptr, const int32_t *d2tot, const int32_t *W,
+                  const int32_t *wlist, int32_t nch, int32_t C, int32_t m, int32_t small_ok,
+                  int32_t *segoff, int32_t *blocksum, int2 *segmap, DevScalars *dev,
+                  cudaStream_t s) {
+  const int32_t nslots = nch * C;
+  if (nslots <= 0) return 0;
+  const int nblocks = div_up(nslots, kScanTile);
+  k_piece_count<<<nblocks, kScanNT, 0, s>>>(a_ptr, d2tot, W, wlist, nslots, C, m, small_ok,
+                                            segoff, blocksum);
+  k_piece_blocks<<<1, kScanNT, 0, s>>>(blocksum, nblocks, nslots, segoff, dev);
+  k_piece_scatter<<<nblocks, kScanNT, 0, s>>>(nslots, blocksum, segoff, segmap);
+  return 3;
 }
 
 int launch_publish(const int32_t *a_ptr, const int32_t *tpos, const int32_t *W,

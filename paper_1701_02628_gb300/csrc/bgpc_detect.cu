@@ -68,22 +68,37 @@ __global__ void __launch_bounds__(kNT) k_kofs(const int32_t *__restrict__ b_ptr,
 }
 
 __global__ void k_trav(const int32_t *__restrict__ a_ptr, const int32_t *__restrict__ W,
-                       const int32_t *__restrict__ d2tot, int32_t m, DevScalars *dev) {
-  unsigned long long acc = 0, inc = 0;
+                       const int32_t *__restrict__ d2tot, int32_t m, int32_t small_ok,
+                       DevScalars *dev) {
+  unsigned long long acc = 0, inc = 0, accl = 0, incl = 0, wl = 0;
   for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < m;
        p += (int64_t)gridDim.x * blockDim.x) {
     const int32_t w = W[p];
     const int32_t deg = a_ptr[w + 1] - a_ptr[w];
-    acc += (unsigned long long)(d2tot[w] - deg);
+    const int32_t d2 = d2tot[w];
+    acc += (unsigned long long)(d2 - deg);
     inc += (unsigned long long)deg;
+    if (!(small_ok && d2 <= kSmallD2 && deg <= kSmallMaxDeg)) {
+      accl += (unsigned long long)(d2 - deg);
+      incl += (unsigned long long)deg;
+      wl++;
+    }
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     acc += __shfl_xor_sync(kFull, acc, o);
     inc += __shfl_xor_sync(kFull, inc, o);
+    accl += __shfl_xor_sync(kFull, accl, o);
+    incl += __shfl_xor_sync(kFull, incl, o);
+    wl += __shfl_xor_sync(kFull, wl, o);
   }
-  if ((threadIdx.x & 31) == 0 && acc) atomicAdd(&dev->trav, acc);
-  if ((threadIdx.x & 31) == 0 && inc) atomicAdd(&dev->incid, inc);
+  if ((threadIdx.x & 31) == 0) {
+    if (acc) atomicAdd(&dev->trav, acc);
+    if (inc) atomicAdd(&dev->incid, inc);
+    if (accl) atomicAdd(&dev->trav_large, accl);
+    if (incl) atomicAdd(&dev->incid_large, incl);
+    if (wl) atomicAdd(&dev->w_large, wl);
+  }
 }
 
 // Warp tier: one warp per net with at most 32 members.  Members outside W
@@ -272,11 +287,11 @@ int launch_kofs(const int32_t *b_ptr, const int32_t *, const int32_t *npos, cons
 }
 
 int launch_trav(const int32_t *a_ptr, const int32_t *W, const int32_t *d2tot, int32_t m,
-                 DevScalars *dev, cudaStream_t s) {
+                int32_t small_ok, DevScalars *dev, cudaStream_t s) {
   if (m <= 0) return 0;
   int grid = div_up(m, kNT);
   if (grid > 1184) grid = 1184;
-  k_trav<<<grid, kNT, 0, s>>>(a_ptr, W, d2tot, m, dev);
+  k_trav<<<grid, kNT, 0, s>>>(a_ptr, W, d2tot, m, small_ok, dev);
   return 1;
 }
 

@@ -36,7 +36,9 @@ enum : int32_t {
 constexpr int kMaxChunk = 64;       // C <= 64: adjacency masks are 64-bit
 constexpr int kSmallWindow = 512;   // bits of the per-vertex small-path window
 constexpr int kSmallD2 = 448;       // small path: sum of net sizes <= this
-constexpr int kPairCap = 1024;      // small path: (vertex, net) pairs per chunk
+constexpr int kSmallMaxDeg = 16;    // small path: at most this many nets
+constexpr int kPairCap = kMaxChunk * kSmallMaxDeg;  // (vertex, net) pairs per chunk
+constexpr int kPiece = 16;          // gather work item: up to this many nets of one vertex
 constexpr int kDetectWarpMax = 32;  // nets up to this size use the warp tier
 
 // Device scalars shared by the kernels of one call.
@@ -48,9 +50,10 @@ struct DevScalars {
   int32_t nbig_d;    // nets with |vtxs| > kDetectWarpMax
   int32_t maxnet;    // largest net
   int32_t maxcolor;  // for validation / statistics
-  int32_t pad;
+  int32_t nseg;      // gather pieces of the round
   unsigned long long trav;   // traversed two-hop entries of the round
   unsigned long long incid;  // incidences sum over W_r of |nets(w)| of the round
+  unsigned long long trav_large, incid_large, w_large;  // the same over gathered (large) vertices
   unsigned long long acc[4]; // reductions (statistics)
 };
 
@@ -72,6 +75,11 @@ struct bgpc_ctx {
   bgpc::Buf<uint8_t> lose;
   bgpc::Buf<int32_t> blocksum, bigt, bigd;
   bgpc::Buf<int32_t> wlist;            // chunks of the round ordered by wave
+  bgpc::Buf<int32_t> segoff;           // gather pieces: exclusive prefix in wave order
+  bgpc::Buf<int2> segmap;              // gather piece -> (wave-order slot, piece index)
+  bgpc::Buf<uint32_t> gbm;             // per-slot forbidden bitmaps of large vertices
+  bgpc::Buf<unsigned long long> gadj;  // per-slot chunk-mate adjacency of large vertices
+  size_t gbm_zeroed = 0;               // words of gbm known to be zero
   int32_t *h_wlist = nullptr;          // pinned host staging of wlist
   size_t h_wlist_cap = 0;
   bgpc::Buf<int32_t> cptr, cidx;       // D2GC closed neighbourhoods
@@ -141,14 +149,33 @@ struct WaveArgs {
   const int32_t *chunks;       // chunk indices of this wave
   int32_t nchunks;
   int32_t maxnet;
-  int32_t cbw;                 // bytemap capacity in bytes (multiple of 16)
+  int32_t words;               // forbidden-bitmap words per vertex (multiple of 4)
+  int32_t small_ok;            // the small path is usable this round
+  uint32_t *gbm;               // per-slot bitmaps of large vertices (slot = list index*C + i)
+  unsigned long long *gadj;    // per-slot chunk-mate masks of large vertices
 };
-// Returns the dynamic shared memory the wave kernel needs for capacity cbw.
-size_t wave_smem_bytes(int32_t cbw);
-// Largest byte-map capacity the wave kernel can hold in shared memory.
-int32_t wave_max_cbw(int smem_optin);
-cudaError_t launch_color_wave(int policy, const WaveArgs &a, int sms, int smem_optin,
-                              cudaStream_t s);
+struct GatherArgs {
+  const int32_t *a_ptr, *a_idx, *b_ptr;
+  const int32_t *nc;
+  const int32_t *W;
+  const int32_t *wlist;        // the round's chunks in wave order
+  const int2 *segmap;          // piece -> (wave-order slot, piece index)
+  const int32_t *segoff;       // exclusive prefix of pieces over wave-order slots
+  int32_t m, C;
+  int32_t slot_lo, slot_hi;    // wave-order slots of this wave
+  int32_t words;
+  uint32_t *gbm;
+  unsigned long long *gadj;
+};
+// Largest bitmap (in words) the wave kernels can hold in shared memory.
+int32_t wave_max_words(int smem_optin);
+cudaError_t launch_color_wave(int policy, const WaveArgs &a, int sms, cudaStream_t s);
+cudaError_t launch_gather(const GatherArgs &a, int sms, cudaStream_t s);
+// Per round: pieces per wave-order slot, their prefix and the piece map.
+int launch_pieces(const int32_t *a_ptr, const int32_t *d2tot, const int32_t *W,
+                  const int32_t *wlist, int32_t nch, int32_t C, int32_t m, int32_t small_ok,
+                  int32_t *segoff, int32_t *blocksum, int2 *segmap, DevScalars *dev,
+                  cudaStream_t s);
 int launch_publish(const int32_t *a_ptr, const int32_t *tpos, const int32_t *W,
                    const int32_t *stage, const int32_t *chunks, int32_t nchunks, int32_t C,
                    int32_t m, int32_t *nc, int32_t *colors, DevScalars *dev, int sms,
@@ -166,7 +193,7 @@ int launch_kofs(const int32_t *b_ptr, const int32_t *nc_unused, const int32_t *n
                  const uint8_t *nown, const int32_t *bigt, int32_t nbig, int32_t *kofs,
                  int sms, cudaStream_t s);
 int launch_trav(const int32_t *a_ptr, const int32_t *W, const int32_t *d2tot, int32_t m,
-                 DevScalars *dev, cudaStream_t s);
+                int32_t small_ok, DevScalars *dev, cudaStream_t s);
 int launch_detect(const int32_t *b_ptr, int32_t n_b, const int32_t *nc, const int32_t *npos,
                    const int32_t *bigd, int32_t nbigd, int32_t *dtab, int32_t tabcap,
                    int32_t nslots, uint8_t *lose, int sms, cudaStream_t s);
