@@ -51,8 +51,21 @@ def peaks():
     return 6800.0, "fallback"
 
 
-def make_workload():
+WORKLOADS = {
+    # the benchmark workload: both Jacobian-like graphs of the BGPC configuration
+    "jacobian": WORKLOAD,
+    # smaller cases for profiler captures (same generators, fewer vertices)
+    "chunglu20": "Chung-Lu 2^20x2^20 (mean 16, max 12.5k, exp 2.1), RS(64,16,64) first fit",
+    "stencil": "stencil9 1024x1024, RS(64,16,64) first fit",
+}
+
+
+def make_workload(name="jacobian"):
     import graphgen as gg
+    if name == "chunglu20":
+        return [gg.chung_lu(1 << 20, 16.0, 12500.0, 2.1, seed=2)]
+    if name == "stencil":
+        return [gg.stencil9(1024)]
     return [gg.stencil9(1024), gg.chung_lu(1 << 22, 16.0, 50000.0, 2.1, seed=2)]
 
 
@@ -225,7 +238,7 @@ def run_gpu(args):
     barrier(world)
     import paper_1701_02628_gb300 as bg
 
-    graphs = make_workload()
+    graphs = make_workload(args.workload)
     ctx = bg.Context(local)
     dgs = [bg.DeviceGraph.from_host(g, dev) for g in graphs]
     colors = [torch.empty(g.n_a, dtype=torch.int32, device=dev) for g in graphs]
@@ -293,13 +306,17 @@ def run_gpu(args):
     # end to end through the public API: H2D of the graph from pinned host
     # memory, coloring, D2H of the colors, every step
     host = []
-    for g in graphs:
+    if args.no_e2e:
+        graphs_e2e = []
+    else:
+        graphs_e2e = graphs
+    for g in graphs_e2e:
         arrs = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
                 for a in (g.a_ptr, g.a_idx, g.b_ptr, g.b_idx)]
         host.append(arrs)
-    out_host = [torch.empty(g.n_a, dtype=torch.int32).pin_memory() for g in graphs]
+    out_host = [torch.empty(g.n_a, dtype=torch.int32).pin_memory() for g in graphs_e2e]
     h2d = sum(a.numel() * 4 for arrs in host for a in arrs)
-    d2h = sum(g.n_a * 4 for g in graphs)
+    d2h = sum(g.n_a * 4 for g in graphs_e2e)
 
     def e2e_step():
         for (hg, dg, c, oh) in zip(host, dgs, colors, out_host):
@@ -308,24 +325,27 @@ def run_gpu(args):
             bg.bgpc_color(ctx, dg, c)
             oh.copy_(c, non_blocking=True)
 
-    for _ in range(max(1, args.warmup)):
-        e2e_step()
-    barrier(world)
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(args.steps):
-        e2e_step()
-    e1.record(stream)
-    torch.cuda.synchronize()
-    barrier(world)
-    e_ms = max_over_ranks(world, e0.elapsed_time(e1), dev)
-    e2e_value = world * entries_step * args.steps / (e_ms / 1000.0)
-    for oh, c in zip(out_host, colors):
-        assert torch.equal(oh, c.cpu())
+    e2e = None
+    if graphs_e2e:
+        for _ in range(max(1, args.warmup)):
+            e2e_step()
+        barrier(world)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            e2e_step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier(world)
+        e_ms = max_over_ranks(world, e0.elapsed_time(e1), dev)
+        e2e = {"value": world * entries_step * args.steps / (e_ms / 1000.0), "unit": UNIT,
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+        for oh, c in zip(out_host, colors):
+            assert torch.equal(oh, c.cpu())
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == "jacobian":
         import oracle
         oracle.build()
         cpu = oracle_sample(graphs, args.cpu_budget, os.cpu_count() or 1)
@@ -344,7 +364,8 @@ def run_gpu(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "int32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "l2": "inputs larger than L2 (no flush)",
+            "config": {"workload": WORKLOADS[args.workload],
+                       "l2": "inputs larger than L2 (no flush)",
                        "parallelism": "replicas" if world > 1 else "single GPU",
                        "graphs": per_graph, "phase_ms_per_step": phase_ms},
             "roofline": {"bound": "hbm", "kernel": dom,
@@ -357,8 +378,7 @@ def run_gpu(args):
                          "other": {k: {"ms_per_step": v[0] / args.steps,
                                        "GB_s": (v[1] / (v[0] / 1000.0) / 1e9) if v[0] else 0.0}
                                    for k, v in kern.items()}},
-            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
-                    "d2h_bytes_per_step": d2h},
+            "e2e": e2e,
             "gpu_launches": launches,
             "cpu_baseline": cpu,
             "clocks": clocks,
@@ -377,6 +397,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--workload", default="jacobian", choices=sorted(WORKLOADS))
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     args = ap.parse_args()
     if args.impl == "reference":

@@ -96,7 +96,11 @@ typedef struct {
     int32_t want_balance;    /* 1: fill the color-set statistics of bgpc_stats_t */
     int32_t profile;         /* 1: time each phase with CUDA events on `stream`
                                 (the ms_* fields of bgpc_stats_t) */
-    int32_t reserved[6];
+    int32_t stop_before_removal; /* debug: when stop_after_waves lands on the end
+                                of a round, stop before its conflict removal
+                                (colors = every vertex's tentative color,
+                                stopped_wave = waves) */
+    int32_t reserved[5];
 } bgpc_opts_t;
 
 /* Statistics of one call (host struct). */

@@ -46,7 +46,8 @@ class bgpc_opts_t(ctypes.Structure):
                 ("rank", ctypes.c_void_p), ("max_rounds", ctypes.c_int32),
                 ("validate", ctypes.c_int32), ("stop_after_waves", ctypes.c_int64),
                 ("W_out", ctypes.c_void_p), ("want_balance", ctypes.c_int32),
-                ("profile", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6)]
+                ("profile", ctypes.c_int32), ("stop_before_removal", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 5)]
 
 
 class bgpc_stats_t(ctypes.Structure):
@@ -212,7 +213,7 @@ def bgpc_opts_default() -> bgpc_opts_t:
 
 def make_opts(policy=BGPC_FF, chunk=64, waves=16, big_net=64, rank=None, max_rounds=1000,
               validate=False, stop_after_waves=0, W_out=None, want_balance=False,
-              profile=False) -> bgpc_opts_t:
+              profile=False, stop_before_removal=False) -> bgpc_opts_t:
     o = bgpc_opts_default()
     o.policy, o.chunk, o.waves, o.big_net = policy, chunk, waves, big_net
     o.rank = _ptr(rank)
@@ -222,6 +223,7 @@ def make_opts(policy=BGPC_FF, chunk=64, waves=16, big_net=64, rank=None, max_rou
     o.W_out = _ptr(W_out)
     o.want_balance = int(bool(want_balance))
     o.profile = int(bool(profile))
+    o.stop_before_removal = int(bool(stop_before_removal))
     return o
 
 
@@ -285,3 +287,4 @@ def bgpc_color_sets(ctx: Context, colors: torch.Tensor, max_colors: int, stream=
                                   ctypes.byref(std), _stream(stream)), "bgpc_color_sets")
     return card, dict(n_sets=ns.value, max_card=mx.value, mean_card=mean.value,
                       std_card=std.value)
+

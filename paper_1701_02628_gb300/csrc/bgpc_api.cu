@@ -323,6 +323,17 @@ int color_impl(bgpc_ctx_t *ctx, const bgpc_graph_t &g, const bgpc_opts_t &o, int
       }
       waves_done++;
     }
+    if (o.stop_before_removal && o.stop_after_waves > 0 && waves_done == o.stop_after_waves) {
+      if (o.W_out) CU(cudaMemcpyAsync(o.W_out, W, sizeof(int32_t) * (size_t)m,
+                                      cudaMemcpyDeviceToDevice, s));
+      CU(cudaStreamSynchronize(s));
+      tm.collect();
+      st.rounds = r + 1;
+      st.stopped_m = m;
+      st.stopped_wave = Q;
+      if (stats) *stats = st;
+      return BGPC_STOPPED;
+    }
     // ---- RemoveConflicts and the next work queue
     ev = tm.begin();
     nk += launch_detect(g.b_ptr, n_b, ctx->nc.p, ctx->npos.p, ctx->bigd.p, nbig_d, ctx->dtab.p,
