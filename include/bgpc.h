@@ -161,6 +161,25 @@ int bgpc_color_sets(bgpc_ctx_t *ctx, const int32_t *colors, int32_t n, int64_t *
                     int32_t max_colors, int32_t *n_sets, int32_t *max_card,
                     double *mean_card, double *std_card, void *stream);
 
+/* Color-set statistics that allocate nothing (no counterpart in the paper:
+ * this is a calling convention, not a step of the method).  For callers that
+ * cannot allocate device memory: code running during CUDA graph capture,
+ * code under an allocator that owns the whole device memory budget, and
+ * latency-critical loops that must not enter the allocator.  Same results as
+ * bgpc_color_sets without the cardinality array and without a context: the
+ * histogram lives in a fixed device array of BGPC_NOALLOC_MAX_COLORS 64-bit
+ * counters (8 MiB, held by every GPU that loads the library until exit).
+ * colors: device int32 [n], each in [0, max_colors); max_colors in
+ * [1, BGPC_NOALLOC_MAX_COLORS], else BGPC_EINVAL (also for a color out of
+ * range).  Outputs are host pointers (each may be NULL).  The first call on a
+ * device looks up the array's device address (make it before any stream
+ * capture).  All calls share the array: calls that overlap on the GPU race.
+ * Synchronises `stream`. */
+#define BGPC_NOALLOC_MAX_COLORS (1 << 20)
+int bgpc_color_sets_noalloc(const int32_t *colors, int32_t n, int32_t max_colors,
+                            int32_t *n_sets, int32_t *max_card, double *mean_card,
+                            double *std_card, void *stream);
+
 /* Human-readable text of a status code (static storage). */
 const char *bgpc_strerror(int status);
 

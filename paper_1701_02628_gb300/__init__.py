@@ -68,7 +68,9 @@ class bgpc_stats_t(ctypes.Structure):
 
 
 EXPORTS = ["bgpc_opts_default", "bgpc_ctx_create", "bgpc_ctx_destroy", "bgpc_color",
-           "d2gc_color", "bgpc_validate", "bgpc_color_sets", "bgpc_strerror"]
+           "d2gc_color", "bgpc_validate", "bgpc_color_sets", "bgpc_color_sets_noalloc",
+           "bgpc_strerror"]
+BGPC_NOALLOC_MAX_COLORS = 1 << 20
 
 _lib = None
 
@@ -100,6 +102,10 @@ def load():
     lib.bgpc_color_sets.argtypes = [vp, vp, ctypes.c_int32, vp, ctypes.c_int32, _c_i32p, _c_i32p,
                                     ctypes.POINTER(ctypes.c_double),
                                     ctypes.POINTER(ctypes.c_double), vp]
+    lib.bgpc_color_sets_noalloc.argtypes = [vp, ctypes.c_int32, ctypes.c_int32, _c_i32p, _c_i32p,
+                                            ctypes.POINTER(ctypes.c_double),
+                                            ctypes.POINTER(ctypes.c_double), vp]
+    lib.bgpc_color_sets_noalloc.restype = ctypes.c_int
     lib.bgpc_strerror.argtypes = [ctypes.c_int]
     lib.bgpc_strerror.restype = ctypes.c_char_p
     for name in ("bgpc_ctx_create", "bgpc_ctx_destroy", "bgpc_color", "d2gc_color",
@@ -288,3 +294,16 @@ def bgpc_color_sets(ctx: Context, colors: torch.Tensor, max_colors: int, stream=
     return card, dict(n_sets=ns.value, max_card=mx.value, mean_card=mean.value,
                       std_card=std.value)
 
+
+def bgpc_color_sets_noalloc(colors: torch.Tensor, max_colors: int, stream=None) -> dict:
+    """Color-set statistics without any device allocation
+    (bgpc_color_sets_noalloc): for callers that cannot allocate, e.g. during
+    CUDA graph capture or under a fixed memory budget.  Calls that overlap on
+    the GPU race (they share one fixed scratch array)."""
+    ns, mx = ctypes.c_int32(0), ctypes.c_int32(0)
+    mean, std = ctypes.c_double(0), ctypes.c_double(0)
+    _check(load().bgpc_color_sets_noalloc(_ptr(colors), colors.numel(), max_colors,
+                                          ctypes.byref(ns), ctypes.byref(mx), ctypes.byref(mean),
+                                          ctypes.byref(std), _stream(stream)),
+           "bgpc_color_sets_noalloc")
+    return dict(n_sets=ns.value, max_card=mx.value, mean_card=mean.value, std_card=std.value)
