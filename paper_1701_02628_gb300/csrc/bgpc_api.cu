@@ -76,8 +76,6 @@ int validate_csr(bgpc_ctx_t *ctx, const int32_t *ptr, const int32_t *idx, int32_
   return err_to_status(ctx->host->err);
 }
 
-int32_t round_up16(int64_t x) { return (int32_t)((x + 15) & ~(int64_t)15); }
-
 // Phase timing with CUDA events recorded on the launch stream (opts.profile).
 enum Phase { PH_SETUP = 0, PH_COLOR = 1, PH_PUBLISH = 2, PH_DETECT = 3, PH_GATHER = 4 };
 struct PhaseTimer {

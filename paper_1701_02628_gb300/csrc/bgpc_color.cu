@@ -246,6 +246,82 @@ __device__ __forceinline__ int32_t win_kth_free_down(uint32_t word, int32_t top,
   return __shfl_sync(kFull, res, __ffs(b) - 1);
 }
 
+// ------------------------------------- candidate summaries (warp, global)
+// A large vertex's forbidden set F_S (colors of its two-hop neighbours in the
+// wave snapshot) sits in a global bitmap g of `words` words; colors beyond
+// 32 * words are free.  Its chunk adds at most 63 more colors (the overlay
+// O), so first fit needs only the kCand smallest free colors of F_S, and the
+// reverse first fit needs the free colors of F_S from the k-th below the top
+// on (plus, for overlay colors above that window, one bit of g each).
+constexpr int kCand = 32;
+
+// The kCand smallest colors not in g, ascending, into out[].
+__device__ __forceinline__ void warp_first_free(const uint32_t *__restrict__ g, int32_t words,
+                                                int32_t *out) {
+  const int lane = threadIdx.x & 31;
+  int32_t got = 0;
+  for (int32_t w0 = 0; got < kCand; w0 += 32) {
+    const int32_t wi = w0 + lane;
+    uint32_t fr = (wi < words) ? ~g[wi] : 0xffffffffu;
+    const int32_t cnt = __popc(fr);
+    const int32_t inc = warp_incl_scan(cnt);
+    int32_t r = got + inc - cnt;
+    while (fr && r < kCand) {
+      out[r++] = wi * 32 + __ffs(fr) - 1;
+      fr &= fr - 1u;
+    }
+    got += __shfl_sync(kFull, inc, 31);
+  }
+  __syncwarp();
+}
+
+// Colors not in g counted down from top: the k-th .. (k+kCand-1)-th (0-based)
+// into out[], descending.  Returns how many of them exist (0 if fewer than
+// k + 1 free colors lie in [0, top]).
+__device__ __forceinline__ int32_t warp_kth_free_down(const uint32_t *__restrict__ g,
+                                                      int32_t words, int32_t top, int32_t k,
+                                                      int32_t *out) {
+  const int lane = threadIdx.x & 31;
+  int32_t seen = 0;
+  const int32_t wtop = top >> 5;
+  for (int32_t w0 = wtop; w0 >= 0 && seen < k + kCand; w0 -= 32) {
+    const int32_t wi = w0 - lane;  // lane 0 holds the highest word
+    uint32_t fr = 0u;
+    if (wi >= 0) {
+      fr = (wi < words) ? ~g[wi] : 0xffffffffu;
+      if (wi == wtop) fr &= mask_upto(wi * 32, top);
+    }
+    const int32_t cnt = __popc(fr);
+    const int32_t inc = warp_incl_scan(cnt);
+    int32_t r = seen + inc - cnt;  // rank of this lane's highest free color
+    if (r + cnt > k && r < k + kCand) {
+      while (fr && r < k + kCand) {
+        const int32_t b = 31 - __clz(fr);
+        if (r >= k) out[r - k] = wi * 32 + b;
+        r++;
+        fr &= ~(1u << b);
+      }
+    }
+    seen += __shfl_sync(kFull, inc, 31);
+  }
+  __syncwarp();
+  const int32_t have = seen - k;
+  return have <= 0 ? 0 : (have < kCand ? have : kCand);
+}
+
+// Index of the candidate equal to c in a sorted list (ascending if asc),
+// or -1.
+__device__ __forceinline__ int32_t cand_index(const int32_t *list, int32_t cnt, int32_t c,
+                                              bool asc) {
+  int32_t lo = 0, hi = cnt - 1;
+  while (lo < hi) {
+    const int32_t mid = (lo + hi) >> 1;
+    const bool before = asc ? (list[mid] < c) : (list[mid] > c);
+    if (before) lo = mid + 1; else hi = mid;
+  }
+  return (cnt > 0 && list[lo] == c) ? lo : -1;
+}
+
 // --------------------------------------------------------- resolve kernel
 
 // Whether vertex (d2, deg) takes the fused small path (must agree with the
@@ -267,7 +343,12 @@ __global__ void __launch_bounds__(NT) k_color_wave(WaveArgs a) {
   __shared__ int32_t s_poff[kPairCap + 1];
   __shared__ uint8_t s_pvert[kPairCap];
   __shared__ int32_t s_red[NW + 1];
-  __shared__ int32_t s_state[4];  // col_max, col_next, npairs
+  __shared__ int32_t s_state[4];  // col_max, col_next, npairs, stop
+  constexpr int KC = (POLICY == BGPC_FF) ? kMaxChunk : 1;
+  __shared__ int32_t s_cand[KC][kCand];   // first-fit candidates of large vertices
+  __shared__ int32_t s_rcand[KC][kCand];  // reverse first-fit candidates (descending)
+  __shared__ int32_t s_rcnt[KC];
+  __shared__ unsigned long long s_large;
   extern __shared__ __align__(16) uint32_t s_big[];  // a.words: one large vertex's F
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -317,6 +398,7 @@ __global__ void __launch_bounds__(NT) k_color_wave(WaveArgs a) {
       const unsigned lg0 = __ballot_sync(kFull, i0 < n && !sm0);
       const unsigned lg1 = __ballot_sync(kFull, i1 < n && !sm1);
       const unsigned long long large = ((unsigned long long)lg1 << 32) | lg0;
+      if (lane == 0) s_large = large;
       const unsigned long long m0 = large >> i0;
       s_next[i0] = m0 ? min(i0 + __ffsll((long long)m0) - 1, n) : n;
       const unsigned long long m1 = large >> i1;
@@ -403,45 +485,140 @@ __global__ void __launch_bounds__(NT) k_color_wave(WaveArgs a) {
     }
     __syncthreads();
 
-    // ---- phase B: resolve the chunk's vertices in order
+    // ---- step S (first fit): condense every large vertex's forbidden set
+    const unsigned long long large = s_large;
+    if constexpr (POLICY == BGPC_FF) {
+      for (int32_t iv = warp; iv < n; iv += NW) {
+        if (!((large >> iv) & 1ull)) continue;
+        const int64_t slot = slot0 + iv;
+        const uint32_t *g = a.gbm + slot * a.words;
+        warp_first_free(g, a.words, s_cand[iv]);
+        int32_t rc = 0;
+        if (s_sown[iv] > a.T)
+          rc = warp_kth_free_down(g, a.words, s_sown[iv] - 1, s_k[iv], s_rcand[iv]);
+        if (lane == 0) {
+          s_rcnt[iv] = rc;
+          s_adj[iv] = a.gadj[slot];
+          a.gadj[slot] = 0ull;
+        }
+      }
+      __syncthreads();
+    }
+
+    // ---- phase B: resolve the chunk's vertices in order.  One warp walks the
+    // chunk; it stops only at a vertex that needs the whole CTA (a large
+    // vertex under B1/B2, or a first-fit vertex whose overlay used up its
+    // candidates).
     int32_t i = 0;
     while (i < n) {
-      const int32_t L = s_next[i];
-      if (warp == 0 && i < L) {
+      if (warp == 0) {
         int32_t col_max = s_state[0], col_next = s_state[1];
-        for (int32_t ii = i; ii < L; ii++) {
+        int32_t ii = i;
+        for (; ii < n; ii++) {
+          const bool lg = (large >> ii) & 1ull;
+          if (lg && POLICY != BGPC_FF) break;
           const unsigned long long am = s_adj[ii];
-#pragma unroll
-          for (int h = 0; h < 2; h++) {
-            const int32_t jj = lane + 32 * h;
-            if (jj < ii && ((am >> jj) & 1ull)) {
-              const int32_t c = s_col[jj];
-              if (c < kSmallWindow) atomicOr(&s_bm[ii][c >> 5], 1u << (c & 31));
-            }
-          }
-          __syncwarp();
-          const uint32_t word = (lane < kWords) ? s_bm[ii][lane] : kFull;
           int32_t x = -1;
-          const int32_t so = s_sown[ii];
-          if (so > a.T) x = win_kth_free_down(word, so - 1, s_k[ii]);
-          if (x < 0) {
-            if (POLICY == BGPC_B1) {
-              if ((s_w[ii] & 1) == 0) {
-                x = win_last_free_down(word, col_max);
-                if (x < 0) x = win_first_free_up(word, col_max + 1);
+          if (!lg) {
+#pragma unroll
+            for (int h = 0; h < 2; h++) {
+              const int32_t jj = lane + 32 * h;
+              if (jj < ii && ((am >> jj) & 1ull)) {
+                const int32_t c = s_col[jj];
+                if (c < kSmallWindow) atomicOr(&s_bm[ii][c >> 5], 1u << (c & 31));
+              }
+            }
+            __syncwarp();
+            const uint32_t word = (lane < kWords) ? s_bm[ii][lane] : kFull;
+            const int32_t so = s_sown[ii];
+            if (so > a.T) x = win_kth_free_down(word, so - 1, s_k[ii]);
+            if (x < 0) {
+              if (POLICY == BGPC_B1) {
+                if ((s_w[ii] & 1) == 0) {
+                  x = win_last_free_down(word, col_max);
+                  if (x < 0) x = win_first_free_up(word, col_max + 1);
+                } else {
+                  x = win_first_free_up(word, 0);
+                }
+              } else if (POLICY == BGPC_B2 || POLICY == BGPC_B2X) {
+                x = win_first_free_up(word, col_next);
+                if (x < 0 || x > col_max) x = win_first_free_up(word, 0);
               } else {
                 x = win_first_free_up(word, 0);
               }
-            } else if (POLICY == BGPC_B2 || POLICY == BGPC_B2X) {
-              x = win_first_free_up(word, col_next);
-              if (x < 0 || x > col_max) x = win_first_free_up(word, 0);
-            } else {
-              x = win_first_free_up(word, 0);
             }
-          }
-          if (x < 0) {  // cannot happen within the window bounds
-            if (lane == 0) atomicOr(a.err, ERR_INTERNAL);
-            x = 0;
+            if (x < 0) {  // cannot happen within the window bounds
+              if (lane == 0) atomicOr(a.err, ERR_INTERNAL);
+              x = 0;
+            }
+          } else if constexpr (POLICY == BGPC_FF) {
+            // overlay colors, at most two per lane
+            int32_t oc[2];
+#pragma unroll
+            for (int h = 0; h < 2; h++) {
+              const int32_t jj = lane + 32 * h;
+              oc[h] = (jj < ii && ((am >> jj) & 1ull)) ? s_col[jj] : -1;
+            }
+            bool fallback = false;
+            const int32_t so = s_sown[ii];
+            const int32_t rcnt = (so > a.T) ? s_rcnt[ii] : 0;
+            if (rcnt > 0) {
+              // k-th free color of F_S u O counted down from so - 1: skip the
+              // overlay colors that are free in F_S above the window, and the
+              // window entries that the overlay takes
+              const int32_t *rcd = s_rcand[ii];
+              const int32_t ak = rcd[0];
+              const uint32_t *g = a.gbm + (slot0 + ii) * a.words;
+              // e = distinct overlay colors in (ak, so - 1] that are free in
+              // F_S (two chunk-mates may share a color: F is a set)
+              bool up[2];
+              uint32_t mark = 0u;
+#pragma unroll
+              for (int h = 0; h < 2; h++) {
+                const int32_t c = oc[h];
+                up[h] = false;
+                if (c < 0 || c > so - 1) continue;
+                if (c > ak) {
+                  up[h] = !((g[c >> 5] >> (c & 31)) & 1u);
+                } else {
+                  const int32_t idx = cand_index(rcd, rcnt, c, false);
+                  if (idx >= 0) mark |= 1u << idx;
+                }
+              }
+              const unsigned m0 = __match_any_sync(kFull, up[0] ? oc[0] : -1 - lane);
+              const unsigned m1 = __match_any_sync(kFull, up[1] ? oc[1] : -1 - lane);
+              bool first0 = up[0] && (__ffs(m0) - 1 == lane);
+              bool first1 = up[1] && (__ffs(m1) - 1 == lane);
+              if (__any_sync(kFull, first1)) {
+                for (int kk = 0; kk < 32; kk++) {
+                  const int32_t v0 = __shfl_sync(kFull, up[0] ? oc[0] : INT32_MIN, kk);
+                  if (first1 && v0 == oc[1]) first1 = false;
+                }
+              }
+              const int32_t e = __popc(__ballot_sync(kFull, first0)) +
+                                __popc(__ballot_sync(kFull, first1));
+              mark = __reduce_or_sync(kFull, mark);
+              const uint32_t avail = ~mark & (rcnt == 32 ? 0xffffffffu : ((1u << rcnt) - 1u));
+              if (__popc(avail) > e) {
+                uint32_t av = avail;
+                for (int32_t t = 0; t < e; t++) av &= av - 1u;  // drop the e lowest
+                x = rcd[__ffs(av) - 1];
+              }
+              else if (rcnt == kCand) fallback = true;
+            }
+            if (x < 0 && !fallback) {
+              uint32_t mark = 0u;
+#pragma unroll
+              for (int h = 0; h < 2; h++) {
+                if (oc[h] < 0) continue;
+                const int32_t idx = cand_index(s_cand[ii], kCand, oc[h], true);
+                if (idx >= 0) mark |= 1u << idx;
+              }
+              mark = __reduce_or_sync(kFull, mark);
+              if (mark == 0xffffffffu) fallback = true;
+              else x = s_cand[ii][__ffs(~mark) - 1];
+            }
+            if (fallback) break;
           }
           col_max = max(col_max, x);
           if (POLICY == BGPC_B2) col_next = min(x + 1, col_max / 3 + 1);
@@ -449,20 +626,25 @@ __global__ void __launch_bounds__(NT) k_color_wave(WaveArgs a) {
           if (lane == 0) s_col[ii] = x;
           __syncwarp();
         }
-        if (lane == 0) { s_state[0] = col_max; s_state[1] = col_next; }
+        if (lane == 0) {
+          s_state[0] = col_max;
+          s_state[1] = col_next;
+          s_state[3] = ii;
+        }
       }
       __syncthreads();
+      const int32_t L = s_state[3];
       if (L < n) {
-        // ---- large vertex: its gathered forbidden set (k_gather) into shared
-        // memory, clearing the global copy for the next wave
+        // ---- CTA-wide path: the vertex's gathered forbidden set (k_gather)
+        // in shared memory, searched with block-wide reductions
         const int64_t slot = slot0 + L;
         uint4 *gsrc = reinterpret_cast<uint4 *>(a.gbm + slot * a.words);
         uint4 *sdst = reinterpret_cast<uint4 *>(s_big);
         for (int32_t x = tid; x < (a.words >> 2); x += NT) {
           sdst[x] = gsrc[x];
-          gsrc[x] = make_uint4(0u, 0u, 0u, 0u);
+          if (POLICY != BGPC_FF) gsrc[x] = make_uint4(0u, 0u, 0u, 0u);
         }
-        if (tid == 0) {
+        if (POLICY != BGPC_FF && tid == 0) {
           s_adj[L] = a.gadj[slot];
           a.gadj[slot] = 0ull;
         }
@@ -503,6 +685,14 @@ __global__ void __launch_bounds__(NT) k_color_wave(WaveArgs a) {
       }
       i = L + 1;
     }
+    if constexpr (POLICY == BGPC_FF) {
+      // leave the slots of this chunk's large vertices zero for the next wave
+      for (unsigned long long mk = large; mk; mk &= mk - 1ull) {
+        const int32_t iv = __ffsll((long long)mk) - 1;
+        uint4 *g = reinterpret_cast<uint4 *>(a.gbm + (slot0 + iv) * a.words);
+        for (int32_t x = tid; x < (a.words >> 2); x += NT) g[x] = make_uint4(0u, 0u, 0u, 0u);
+      }
+    }
     if (tid < n) a.stage[p0 + tid] = s_col[tid];
     __syncthreads();
   }
@@ -513,68 +703,135 @@ __global__ void __launch_bounds__(NT) k_color_wave(WaveArgs a) {
 // the colors of the members of those nets (from the snapshot, via nc) into a
 // shared bitmap and the earlier chunk-mates it meets into a 64-bit mask, then
 // ORs both into the vertex's global slot.  A heavy vertex is spread over many
-// CTAs, so no chunk waits for one SM.
+// CTAs, so no chunk waits for one SM.  Inside a piece every warp takes an
+// equal contiguous slice of the piece's entries (net sizes differ by orders
+// of magnitude, so one warp per net would leave most warps waiting) and
+// streams it with 16-byte loads.
+
+// One mirror word: a published color joins the forbidden bitmap; an earlier
+// chunk-mate (queue position in [p0, p0 + rel_hi)) joins the adjacency mask.
+__device__ __forceinline__ void take(int32_t x, uint32_t *s_bm, int32_t lim, int32_t p0,
+                                     int32_t rel_hi, unsigned long long &adj) {
+  if (x >= 0) {
+    if (x < lim) atomicOr(&s_bm[x >> 5], 1u << (x & 31));
+  } else {
+    const int32_t rel = (-2 - x) - p0;
+    if (rel >= 0 && rel < rel_hi) adj |= 1ull << rel;
+  }
+}
+
+// The lanes of a warp stream src[0, n) (scalar head to a 16-byte boundary,
+// int4 body with four loads in flight per lane, scalar tail).
+__device__ __forceinline__ void warp_stream(const int32_t *__restrict__ src, int32_t n,
+                                            uint32_t *s_bm, int32_t lim, int32_t p0,
+                                            int32_t rel_hi, unsigned long long &adj) {
+  const int lane = threadIdx.x & 31;
+  const int32_t mis = (int32_t)((reinterpret_cast<uintptr_t>(src) >> 2) & 3);
+  const int32_t head = mis ? min(n, 4 - mis) : 0;
+  if (lane < head) take(__ldg(src + lane), s_bm, lim, p0, rel_hi, adj);
+  const int4 *v = reinterpret_cast<const int4 *>(src + head);
+  const int32_t nv = (n - head) >> 2;
+  for (int32_t i0 = lane; i0 < nv; i0 += 128) {
+    int4 q[4];
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+      const int32_t i = i0 + 32 * k;
+      q[k] = (i < nv) ? __ldg(v + i) : make_int4(INT32_MIN, INT32_MIN, INT32_MIN, INT32_MIN);
+    }
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+      if (q[k].x == INT32_MIN) continue;
+      take(q[k].x, s_bm, lim, p0, rel_hi, adj);
+      take(q[k].y, s_bm, lim, p0, rel_hi, adj);
+      take(q[k].z, s_bm, lim, p0, rel_hi, adj);
+      take(q[k].w, s_bm, lim, p0, rel_hi, adj);
+    }
+  }
+  const int32_t t0 = head + (nv << 2);
+  if (t0 + lane < n) take(__ldg(src + t0 + lane), s_bm, lim, p0, rel_hi, adj);
+}
+
 template <int NT>
 __global__ void __launch_bounds__(NT) k_gather(GatherArgs a) {
   constexpr int NW = NT / 32;
   extern __shared__ __align__(16) uint32_t s_bm[];
+  __shared__ int32_t s_pstart[kPiece];
+  __shared__ int32_t s_poff[kPiece + 1];
+  __shared__ int32_t s_info[4];  // p0, rel_hi, whole, nnets
+  __shared__ int64_t s_slot;
   __shared__ unsigned long long s_adj;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int32_t sbeg = a.segoff[a.slot_lo], send = a.segoff[a.slot_hi];
   const int32_t lim = a.words * 32;
+  for (int32_t x = tid; x < a.words; x += NT) s_bm[x] = 0u;
+  if (tid == 0) s_adj = 0ull;
   for (int32_t sg = sbeg + (int32_t)blockIdx.x; sg < send; sg += (int32_t)gridDim.x) {
-    const int2 sm = a.segmap[sg];
-    const int32_t u = sm.x, piece = sm.y;  // wave-order slot, piece of the vertex
-    const int32_t j = a.wlist[u / a.C];
-    const int32_t p0 = j * a.C;
-    const int32_t p = p0 + u % a.C;
-    const int32_t w = a.W[p];
-    const int32_t ibeg = a.a_ptr[w] + piece * kPiece;
-    const int32_t iend = min(a.a_ptr[w + 1], ibeg + kPiece);
-    const bool whole = (a.segoff[u + 1] - a.segoff[u]) == 1;
-    for (int32_t x = tid; x < a.words; x += NT) s_bm[x] = 0u;
-    if (tid == 0) s_adj = 0ull;
-    __syncthreads();
-    const int32_t rel_hi = p - p0;
-    unsigned long long adj = 0ull;
-    int bad = 0;
-    for (int32_t it = ibeg + warp; it < iend; it += NW) {
-      const int32_t v = a.a_idx[it];
-      const int32_t beg = a.b_ptr[v], end = a.b_ptr[v + 1];
-      for (int32_t e0 = beg + lane; e0 < end; e0 += 128) {
-        int32_t val[4];
-#pragma unroll
-        for (int q = 0; q < 4; q++) {
-          const int32_t e = e0 + 32 * q;
-          val[q] = (e < end) ? a.nc[e] : INT32_MIN;
-        }
-#pragma unroll
-        for (int q = 0; q < 4; q++) {
-          const int32_t x = val[q];
-          if (x == INT32_MIN) continue;
-          if (x >= 0) {
-            if (x < lim) atomicOr(&s_bm[x >> 5], 1u << (x & 31)); else bad = 1;
-          } else {
-            const int32_t rel = (-2 - x) - p0;
-            if (rel >= 0 && rel < rel_hi) adj |= 1ull << rel;
-          }
-        }
+    // ---- the piece: its vertex and the prefix of its net sizes
+    if (warp == 0) {
+      const int2 sm = a.segmap[sg];
+      const int32_t u = sm.x, piece = sm.y;  // wave-order slot, piece of the vertex
+      const int32_t j = a.wlist[u / a.C];
+      const int32_t p0 = j * a.C;
+      const int32_t p = p0 + u % a.C;
+      const int32_t w = a.W[p];
+      const int32_t ibeg = a.a_ptr[w] + piece * kPiece;
+      const int32_t nnets = min(a.a_ptr[w + 1] - ibeg, kPiece);
+      int32_t sz = 0, bp = 0;
+      if (lane < nnets) {
+        const int32_t v = a.a_idx[ibeg + lane];
+        bp = a.b_ptr[v];
+        sz = a.b_ptr[v + 1] - bp;
+      }
+      const int32_t inc = warp_incl_scan(sz);
+      if (lane < kPiece) {
+        s_pstart[lane] = bp;
+        s_poff[lane + 1] = inc;
+      }
+      if (lane == 0) {
+        s_poff[0] = 0;
+        s_info[0] = p0;
+        s_info[1] = p - p0;
+        s_info[2] = (a.segoff[u + 1] - a.segoff[u]) == 1;
+        s_info[3] = nnets;
+        s_slot = (int64_t)(u - a.slot_lo);
       }
     }
-    (void)bad;
-    if (adj) atomicOr(&s_adj, adj);
     __syncthreads();
-    const int64_t slot = (int64_t)(u - a.slot_lo);
-    uint32_t *g = a.gbm + slot * a.words;
-    if (whole) {
-      for (int32_t x = tid; x < a.words; x += NT) g[x] = s_bm[x];
-      if (tid == 0) a.gadj[slot] = s_adj;
-    } else {
-      for (int32_t x = tid; x < a.words; x += NT) {
-        const uint32_t b = s_bm[x];
-        if (b) atomicOr(&g[x], b);
+    const int32_t p0 = s_info[0], rel_hi = s_info[1], nnets = s_info[3];
+    const int32_t E = s_poff[nnets];
+    const int32_t per = (E + NW - 1) / NW;
+    const int32_t lo_e = min(E, warp * per), hi_e = min(E, lo_e + per);
+    unsigned long long adj = 0ull;
+    if (lo_e < hi_e) {
+      int32_t t = 0;  // first net of the slice: largest t with s_poff[t] <= lo_e
+      for (int32_t step = 8; step > 0; step >>= 1)
+        if (t + step < nnets && s_poff[t + step] <= lo_e) t += step;
+      for (; t < nnets && s_poff[t] < hi_e; t++) {
+        const int32_t nb = max(lo_e, s_poff[t]), ne = min(hi_e, s_poff[t + 1]);
+        warp_stream(a.nc + s_pstart[t] + (nb - s_poff[t]), ne - nb, s_bm, lim, p0, rel_hi, adj);
       }
-      if (tid == 0 && s_adj) atomicOr(&a.gadj[slot], s_adj);
+    }
+    const unsigned lo32 = __reduce_or_sync(kFull, (unsigned)(adj & 0xffffffffull));
+    const unsigned hi32 = __reduce_or_sync(kFull, (unsigned)(adj >> 32));
+    if (lane == 0 && (lo32 | hi32)) atomicOr(&s_adj, ((unsigned long long)hi32 << 32) | lo32);
+    __syncthreads();
+    // ---- merge into the vertex's slot, leaving the shared bitmap zero
+    const int64_t slot = s_slot;
+    uint32_t *g = a.gbm + slot * a.words;
+    const bool whole = s_info[2] != 0;
+    for (int32_t x = tid; x < a.words; x += NT) {
+      const uint32_t b = s_bm[x];
+      if (b) {
+        if (whole) g[x] = b; else atomicOr(&g[x], b);
+        s_bm[x] = 0u;
+      }
+    }
+    if (tid == 0) {
+      const unsigned long long m = s_adj;
+      if (m) {
+        if (whole) a.gadj[slot] = m; else atomicOr(&a.gadj[slot], m);
+      }
+      s_adj = 0ull;
     }
     __syncthreads();
   }
