@@ -227,6 +227,47 @@ def run_reference(args):
 
 # ----------------------------------------------------------------- GPU leg
 
+def learned_order_report(bg, ctx, dev, chung_lu_dg):
+    """The learned vertex order (features -> MLP -> rank) against id order:
+    trained on 16 graphs of the batched workload (seed 23), evaluated on the
+    Chung-Lu 2^22 graph and on 64 fresh graphs of the batched workload
+    (seed 29, |V_A| log-uniform in [1e3, 1e6]).  Reports colors used."""
+    import torch
+    import graphgen as gg
+    train = [bg.DeviceGraph.from_host(gg.batch_graph(23, i, lo=1e3, hi=1e5), dev)
+             for i in range(16)]
+    t0 = time.time()
+    mlp, losses = bg.train_order(ctx, train, torch.from_numpy(gg.mlp_init(7)).to(dev),
+                                 steps=300, lr=3e-3)
+    torch.cuda.synchronize()
+    t_train = time.time() - t0
+
+    def colors(dg, rank=None):
+        _, st, _ = bg.bgpc_color(ctx, dg, rank=rank)
+        return st["colors"]
+
+    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s0.record()
+    rank = bg.learned_rank(ctx, chung_lu_dg, mlp)
+    s1.record()
+    torch.cuda.synchronize()
+    cl = {"colors_id": colors(chung_lu_dg), "colors_learned": colors(chung_lu_dg, rank),
+          "ms_order": s0.elapsed_time(s1)}
+    fresh_id, fresh_l = [], []
+    for i in range(64):
+        dg = bg.DeviceGraph.from_host(gg.batch_graph(29, i), dev)
+        fresh_id.append(colors(dg))
+        fresh_l.append(colors(dg, bg.learned_rank(ctx, dg, mlp)))
+    return {"model": "MLP 8-64-64-1, bf16 weights, fp32 arithmetic, Adam",
+            "train": {"graphs": 16, "steps": len(losses), "loss_first": losses[0],
+                      "loss_last": losses[-1], "seconds": t_train},
+            "chung_lu_2^22": cl,
+            "fresh_batch_graphs": {"graphs": 64, "colors_id_mean": float(np.mean(fresh_id)),
+                                   "colors_learned_mean": float(np.mean(fresh_l)),
+                                   "fewer_colors": int(sum(a > b for a, b in zip(fresh_id, fresh_l))),
+                                   "more_colors": int(sum(a < b for a, b in zip(fresh_id, fresh_l)))}}
+
+
 def run_gpu(args):
     import torch
     world, rank, local = dist_setup()
@@ -344,6 +385,10 @@ def run_gpu(args):
         for oh, c in zip(out_host, colors):
             assert torch.equal(oh, c.cpu())
 
+    learned = None
+    if rank == 0 and not args.no_learned and args.workload == "jacobian":
+        learned = learned_order_report(bg, ctx, dev, dgs[1])
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == "jacobian":
         import oracle
@@ -382,6 +427,7 @@ def run_gpu(args):
             "gpu_launches": launches,
             "cpu_baseline": cpu,
             "clocks": clocks,
+            "learned_order": learned,
         }
         print(json.dumps(line), flush=True)
     ctx.close()
@@ -398,6 +444,7 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--workload", default="jacobian", choices=sorted(WORKLOADS))
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     args = ap.parse_args()

@@ -192,3 +192,16 @@ def batch_graph(seed: int, index: int, lo: float = 1e3, hi: float = 1e6,
     return _take(_load().gg_batch_graph(seed, index, lo, hi, lam, maxdeg),
                  f"batch_s{seed}_{index}", False)
 
+
+
+def mlp_init(seed: int):
+    """Initial parameters [4801] (float32) of the order model 8 -> 64 -> 64 -> 1,
+    packed W1[64][8], b1[64], W2[64][64], b2[64], W3[64], b3: every weight and
+    bias of a layer with fan-in f drawn uniform in [-1/sqrt(f), 1/sqrt(f)]
+    (numpy PCG64 stream of ``seed``)."""
+    rng = np.random.default_rng([0x6d6c70, seed])
+    parts = []
+    for fan_in, count in ((8, 64 * 8 + 64), (64, 64 * 64 + 64), (64, 64 + 1)):
+        b = 1.0 / np.sqrt(fan_in)
+        parts.append(rng.uniform(-b, b, count))
+    return np.concatenate(parts).astype(np.float32)

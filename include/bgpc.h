@@ -180,6 +180,69 @@ int bgpc_color_sets_noalloc(const int32_t *colors, int32_t n, int32_t max_colors
                             int32_t *n_sets, int32_t *max_card, double *mean_card,
                             double *std_card, void *stream);
 
+/* ---- learned vertex order ---------------------------------------------
+ * The paper colors in a given vertex order and discusses how static orders
+ * (natural, smallest-last) change the number of colors (Sec. VI, Table II).
+ * These calls build an order from a small regression model instead: per
+ * vertex features -> MLP 8 -> 64 -> 64 -> 1 (ReLU, bfloat16 weights, float32
+ * arithmetic) -> score -> rank (decreasing score first); the rank is then
+ * passed as bgpc_opts_t.rank.  The model itself is not in the paper.
+ *
+ * Parameter packing (float, 4801 values): W1[64][8] at 0, b1[64] at 512,
+ * W2[64][64] at 576, b2[64] at 4672, W3[64] at 4736, b3 at 4800 (row-major,
+ * row = output unit).  z1 = W1 x + b1, h1 = relu(z1), z2 = W2 h1 + b2,
+ * h2 = relu(z2), score = W3 . h2 + b3, computed with the bfloat16 values of
+ * the weights (w_bf16). */
+#define BGPC_MLP_IN 8
+#define BGPC_MLP_HIDDEN 64
+#define BGPC_MLP_PARAMS 4801
+
+typedef struct {
+    float *w;           /* device [4801]: float32 master parameters, caller-initialised */
+    uint16_t *w_bf16;   /* device [4801]: their bfloat16 values (bgpc_mlp_sync) */
+    float *adam_m;      /* device [4801]: Adam first moments, caller-zeroed */
+    float *adam_v;      /* device [4801]: Adam second moments, caller-zeroed */
+    int64_t step;       /* (host) Adam steps taken so far, caller-zeroed */
+} bgpc_mlp_t;
+
+/* Features X (device float [n_a][8]) of every V_A vertex w, from the sizes
+ * s_v = |vtxs(v)| of its nets: log1p of |nets(w)|, mean s, max s, sum s,
+ * sum (s - 1) (the two-hop volume of Sec. III), min s, #{v : s_v > big_net},
+ * sum s^2 / sum s.  A vertex with no nets gets zeros.  big_net >= 0. */
+int bgpc_features(bgpc_ctx_t *ctx, const bgpc_graph_t *g, int32_t big_net, float *X,
+                  void *stream);
+
+/* w_bf16 <- bfloat16(w), round to nearest even (call after writing w). */
+int bgpc_mlp_sync(bgpc_ctx_t *ctx, const bgpc_mlp_t *mlp, void *stream);
+
+/* score (device float [n]) of the rows of X (device float [n][8]). */
+int bgpc_mlp_forward(bgpc_ctx_t *ctx, const bgpc_mlp_t *mlp, const float *X, int32_t n,
+                     float *score, void *stream);
+
+/* Gradient (device float [4801]) of L = mean_i (score_i - y_i)^2 with respect
+ * to the (bfloat16-valued) parameters, and *loss = L (host, may be NULL).
+ * Deterministic: the reduction order does not depend on timing.  n >= 1.
+ * Synchronises `stream` when loss is not NULL. */
+int bgpc_mlp_grad(bgpc_ctx_t *ctx, const bgpc_mlp_t *mlp, const float *X, const float *y,
+                  int32_t n, float *grad, float *loss, void *stream);
+
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected) on w with
+ * the gradient grad (device float [4801]); increments mlp->step, refreshes
+ * w_bf16. */
+int bgpc_mlp_adam(bgpc_ctx_t *ctx, bgpc_mlp_t *mlp, const float *grad, float lr, void *stream);
+
+/* bgpc_mlp_grad followed by bgpc_mlp_adam (the gradient in context scratch);
+ * *loss (host, may be NULL) is the loss before the step. */
+int bgpc_mlp_train_step(bgpc_ctx_t *ctx, bgpc_mlp_t *mlp, const float *X, const float *y,
+                        int32_t n, float lr, float *loss, void *stream);
+
+/* rank (device int32 [n]) = position of every index in the order of
+ * decreasing score (device float [n]), equal scores by increasing index;
+ * -0.0 and +0.0 are equal; a NaN score is BGPC_EINVAL.  A stable LSD radix
+ * sort on order-preserving 32-bit keys.  Synchronises `stream`. */
+int bgpc_rank_from_scores(bgpc_ctx_t *ctx, const float *score, int32_t n, int32_t *rank,
+                          void *stream);
+
 /* Human-readable text of a status code (static storage). */
 const char *bgpc_strerror(int status);
 

@@ -38,23 +38,29 @@ N_PARAMS = 4801
 BETA1, BETA2, EPS = 0.9, 0.999, 1e-8
 
 
-def features(g, big_net: int) -> np.ndarray:
-    """X[n_a, 8] (float64): for vertex w with net sizes s_v, v in nets(w):
-    log1p of deg, mean s, max s, sum s, sum (s - 1), min s, #{s > T},
-    sum s^2 / sum s.  A vertex with no nets has all-zero features."""
+def features_of(g, vertices, big_net: int) -> np.ndarray:
+    """Features (float64) of the listed vertices: for vertex w with net sizes
+    s_v, v in nets(w): log1p of deg, mean s, max s, sum s, sum (s - 1),
+    min s, #{s > T}, sum s^2 / sum s.  A vertex with no nets has all-zero
+    features."""
     sizes = np.diff(np.asarray(g.b_ptr, np.int64)).astype(np.float64)
-    X = np.zeros((g.n_a, N_IN))
     a_ptr = np.asarray(g.a_ptr, np.int64)
     a_idx = np.asarray(g.a_idx, np.int64)
-    for w in range(g.n_a):
+    X = np.zeros((len(vertices), N_IN))
+    for r, w in enumerate(vertices):
         s = sizes[a_idx[a_ptr[w]:a_ptr[w + 1]]]
         if s.size == 0:
             continue
         tot = s.sum()
         raw = [s.size, tot / s.size, s.max(), tot, (s - 1).sum(), s.min(),
                float((s > big_net).sum()), (s * s).sum() / tot]
-        X[w] = np.log1p(raw)
+        X[r] = np.log1p(raw)
     return X
+
+
+def features(g, big_net: int) -> np.ndarray:
+    """X[n_a, 8] (float64): ``features_of`` every vertex of V_A."""
+    return features_of(g, range(g.n_a), big_net)
 
 
 def bf16(x32: np.ndarray) -> np.ndarray:

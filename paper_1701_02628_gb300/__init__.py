@@ -69,7 +69,15 @@ class bgpc_stats_t(ctypes.Structure):
 
 EXPORTS = ["bgpc_opts_default", "bgpc_ctx_create", "bgpc_ctx_destroy", "bgpc_color",
            "d2gc_color", "bgpc_validate", "bgpc_color_sets", "bgpc_color_sets_noalloc",
-           "bgpc_strerror"]
+           "bgpc_features", "bgpc_mlp_sync", "bgpc_mlp_forward", "bgpc_mlp_grad",
+           "bgpc_mlp_adam", "bgpc_mlp_train_step", "bgpc_rank_from_scores", "bgpc_strerror"]
+MLP_IN, MLP_HIDDEN, MLP_PARAMS = 8, 64, 4801
+
+
+class bgpc_mlp_t(ctypes.Structure):
+    _fields_ = [("w", ctypes.c_void_p), ("w_bf16", ctypes.c_void_p),
+                ("adam_m", ctypes.c_void_p), ("adam_v", ctypes.c_void_p),
+                ("step", ctypes.c_int64)]
 BGPC_NOALLOC_MAX_COLORS = 1 << 20
 
 _lib = None
@@ -106,6 +114,18 @@ def load():
                                             ctypes.POINTER(ctypes.c_double),
                                             ctypes.POINTER(ctypes.c_double), vp]
     lib.bgpc_color_sets_noalloc.restype = ctypes.c_int
+    M = ctypes.POINTER(bgpc_mlp_t)
+    fp = ctypes.POINTER(ctypes.c_float)
+    lib.bgpc_features.argtypes = [vp, ctypes.POINTER(bgpc_graph_t), ctypes.c_int32, vp, vp]
+    lib.bgpc_mlp_sync.argtypes = [vp, M, vp]
+    lib.bgpc_mlp_forward.argtypes = [vp, M, vp, ctypes.c_int32, vp, vp]
+    lib.bgpc_mlp_grad.argtypes = [vp, M, vp, vp, ctypes.c_int32, vp, fp, vp]
+    lib.bgpc_mlp_adam.argtypes = [vp, M, vp, ctypes.c_float, vp]
+    lib.bgpc_mlp_train_step.argtypes = [vp, M, vp, vp, ctypes.c_int32, ctypes.c_float, fp, vp]
+    lib.bgpc_rank_from_scores.argtypes = [vp, vp, ctypes.c_int32, vp, vp]
+    for name in ("bgpc_features", "bgpc_mlp_sync", "bgpc_mlp_forward", "bgpc_mlp_grad",
+                 "bgpc_mlp_adam", "bgpc_mlp_train_step", "bgpc_rank_from_scores"):
+        getattr(lib, name).restype = ctypes.c_int
     lib.bgpc_strerror.argtypes = [ctypes.c_int]
     lib.bgpc_strerror.restype = ctypes.c_char_p
     for name in ("bgpc_ctx_create", "bgpc_ctx_destroy", "bgpc_color", "d2gc_color",
@@ -137,12 +157,16 @@ def _stream(stream):
     return ctypes.c_void_p(stream.cuda_stream)
 
 
-def _ptr(t):
+def _ptr(t, dtype=torch.int32):
     if t is None:
         return None
-    if t.dtype != torch.int32 or not t.is_cuda or not t.is_contiguous():
-        raise TypeError("expected a contiguous int32 CUDA tensor")
+    if t.dtype != dtype or not t.is_cuda or not t.is_contiguous():
+        raise TypeError(f"expected a contiguous {dtype} CUDA tensor")
     return ctypes.c_void_p(t.data_ptr())
+
+
+def _fptr(t):
+    return _ptr(t, torch.float32)
 
 
 class Context:
@@ -307,3 +331,129 @@ def bgpc_color_sets_noalloc(colors: torch.Tensor, max_colors: int, stream=None) 
                                           ctypes.byref(std), _stream(stream)),
            "bgpc_color_sets_noalloc")
     return dict(n_sets=ns.value, max_card=mx.value, mean_card=mean.value, std_card=std.value)
+
+
+# ------------------------------------------------------------ learned order
+
+class MLP:
+    """Parameters of the order model (bgpc_mlp_t): float32 master weights w,
+    their bfloat16 values (as int16 storage), Adam moments and step count,
+    all on one CUDA device.  ``params`` is the packed float32 vector [4801]
+    (W1[64][8], b1[64], W2[64][64], b2[64], W3[64], b3)."""
+
+    def __init__(self, ctx: "Context", params: torch.Tensor, stream=None):
+        if params.numel() != MLP_PARAMS:
+            raise ValueError("expected 4801 parameters")
+        dev = params.device if params.is_cuda else torch.device("cuda", ctx.device)
+        self.w = params.detach().to(dev, torch.float32).contiguous().clone()
+        self.w_bf16 = torch.empty(MLP_PARAMS, dtype=torch.int16, device=dev)
+        self.adam_m = torch.zeros(MLP_PARAMS, dtype=torch.float32, device=dev)
+        self.adam_v = torch.zeros(MLP_PARAMS, dtype=torch.float32, device=dev)
+        self.step = 0
+        self.sync(ctx, stream)
+
+    def c_struct(self) -> bgpc_mlp_t:
+        return bgpc_mlp_t(self.w.data_ptr(), self.w_bf16.data_ptr(), self.adam_m.data_ptr(),
+                          self.adam_v.data_ptr(), self.step)
+
+    def sync(self, ctx: "Context", stream=None):
+        """Refresh the bfloat16 copy after writing ``w`` (bgpc_mlp_sync)."""
+        m = self.c_struct()
+        _check(load().bgpc_mlp_sync(ctx.handle, ctypes.byref(m), _stream(stream)),
+               "bgpc_mlp_sync")
+
+    def bf16_values(self) -> torch.Tensor:
+        """The weights the forward pass uses, as float32 values."""
+        return (self.w_bf16.to(torch.int32) << 16).view(torch.float32)
+
+
+def features(ctx: Context, g: DeviceGraph, big_net: int = 64, out=None, stream=None):
+    """Per-vertex features X [n_a, 8] (bgpc_features)."""
+    X = out if out is not None else torch.empty((g.n_a, MLP_IN), dtype=torch.float32,
+                                                device=g.a_ptr.device)
+    gs = g.c_struct()
+    _check(load().bgpc_features(ctx.handle, ctypes.byref(gs), big_net,
+                                _fptr(X) if g.n_a else None, _stream(stream)), "bgpc_features")
+    return X
+
+
+def mlp_forward(ctx: Context, mlp: MLP, X: torch.Tensor, out=None, stream=None):
+    """Scores [n] of the rows of X (bgpc_mlp_forward)."""
+    n = X.shape[0]
+    s = out if out is not None else torch.empty(n, dtype=torch.float32, device=X.device)
+    m = mlp.c_struct()
+    _check(load().bgpc_mlp_forward(ctx.handle, ctypes.byref(m), _fptr(X) if n else None, n,
+                                   _fptr(s) if n else None, _stream(stream)), "bgpc_mlp_forward")
+    return s
+
+
+def mlp_grad(ctx: Context, mlp: MLP, X: torch.Tensor, y: torch.Tensor, stream=None):
+    """(gradient [4801], loss) of the mean squared error (bgpc_mlp_grad)."""
+    g = torch.empty(MLP_PARAMS, dtype=torch.float32, device=X.device)
+    loss = ctypes.c_float(0)
+    m = mlp.c_struct()
+    _check(load().bgpc_mlp_grad(ctx.handle, ctypes.byref(m), _fptr(X), _fptr(y), X.shape[0],
+                                _fptr(g), ctypes.byref(loss), _stream(stream)), "bgpc_mlp_grad")
+    return g, loss.value
+
+
+def mlp_adam(ctx: Context, mlp: MLP, grad: torch.Tensor, lr: float, stream=None):
+    """One Adam step with the given gradient (bgpc_mlp_adam)."""
+    m = mlp.c_struct()
+    _check(load().bgpc_mlp_adam(ctx.handle, ctypes.byref(m), _fptr(grad), lr, _stream(stream)),
+           "bgpc_mlp_adam")
+    mlp.step = m.step
+
+
+def mlp_train_step(ctx: Context, mlp: MLP, X: torch.Tensor, y: torch.Tensor, lr: float,
+                   stream=None) -> float:
+    """Gradient and Adam step (bgpc_mlp_train_step); returns the loss before the step."""
+    loss = ctypes.c_float(0)
+    m = mlp.c_struct()
+    _check(load().bgpc_mlp_train_step(ctx.handle, ctypes.byref(m), _fptr(X), _fptr(y),
+                                      X.shape[0], lr, ctypes.byref(loss), _stream(stream)),
+           "bgpc_mlp_train_step")
+    mlp.step = m.step
+    return loss.value
+
+
+def rank_from_scores(ctx: Context, score: torch.Tensor, out=None, stream=None):
+    """rank [n] int32: position in the order of decreasing score, ties by index
+    (bgpc_rank_from_scores)."""
+    n = score.numel()
+    r = out if out is not None else torch.empty(n, dtype=torch.int32, device=score.device)
+    _check(load().bgpc_rank_from_scores(ctx.handle, _fptr(score) if n else None, n,
+                                        _ptr(r) if n else None, _stream(stream)),
+           "bgpc_rank_from_scores")
+    return r
+
+
+def learned_rank(ctx: Context, g: DeviceGraph, mlp: MLP, big_net: int = 64, stream=None):
+    """features -> MLP score -> rank, ready for bgpc_color(..., rank=...)."""
+    X = features(ctx, g, big_net, stream=stream)
+    return rank_from_scores(ctx, mlp_forward(ctx, mlp, X, stream=stream), stream=stream)
+
+
+def order_target(ctx: Context, g: DeviceGraph, stream=None, **opts) -> torch.Tensor:
+    """Training target of the order model for graph g: the color every vertex
+    gets from a plain first-fit coloring in id order, divided by the number
+    of colors (vertices that end up in high colors are the hard ones, and the
+    learned order colors them first)."""
+    c, st, _ = bgpc_color(ctx, g, stream=stream, **opts)
+    return c.to(torch.float32) / float(max(st["colors"], 1))
+
+
+def train_order(ctx: Context, graphs, params: torch.Tensor, steps: int = 200,
+                lr: float = 3e-3, big_net: int = 64, stream=None):
+    """Fit the order model on the given graphs: features and targets of every
+    graph, concatenated, then ``steps`` full-batch Adam steps (every step is
+    bgpc_mlp_train_step).  Returns (MLP, list of losses)."""
+    Xs, ys = [], []
+    for g in graphs:
+        Xs.append(features(ctx, g, big_net, stream=stream))
+        ys.append(order_target(ctx, g, stream=stream))
+    X = torch.cat(Xs).contiguous()
+    y = torch.cat(ys).contiguous()
+    mlp = MLP(ctx, params, stream)
+    losses = [mlp_train_step(ctx, mlp, X, y, lr, stream) for _ in range(steps)]
+    return mlp, losses

@@ -451,6 +451,8 @@ int bgpc_ctx_destroy(bgpc_ctx_t *ctx) {
   release(ctx->gadj);
   if (ctx->h_wlist) cudaFreeHost(ctx->h_wlist);
   release(ctx->card); release(ctx->bad);
+  release(ctx->rkey0); release(ctx->rkey1); release(ctx->rval0); release(ctx->rval1);
+  release(ctx->rhist); release(ctx->rsum); release(ctx->mpart); release(ctx->mgrad);
   for (cudaEvent_t e : ctx->events) cudaEventDestroy(e);
   ctx->events.clear();
   if (ctx->dev) cudaFree(ctx->dev);

@@ -88,6 +88,12 @@ struct bgpc_ctx {
   size_t dtab_filled = 0;              // entries of dtab already set to INT_MAX
   bgpc::Buf<unsigned long long> card;  // color-set cardinalities
   bgpc::Buf<uint8_t> bad;              // validation flags
+  bgpc::Buf<uint32_t> rkey0, rkey1;    // rank_from_scores: radix-sort keys (ping-pong)
+  bgpc::Buf<int32_t> rval0, rval1;     // ... and the indices they carry
+  bgpc::Buf<int32_t> rhist;            // ... per-tile digit counts, then their offsets
+  bgpc::Buf<int32_t> rsum;             // ... scan block sums
+  bgpc::Buf<float> mpart;              // MLP gradient: per-block partial sums
+  bgpc::Buf<float> mgrad;              // MLP gradient (train step)
   bgpc::DevScalars *dev = nullptr;     // device scalars
   std::vector<cudaEvent_t> events;     // phase timing (opts.profile)
   bgpc::DevScalars *host = nullptr;    // pinned mirror

@@ -67,3 +67,35 @@ def test_ctx_create_without_gpu_fails_cleanly(lib):
     h = ctypes.c_void_p()
     lib.bgpc_ctx_create.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int]
     assert lib.bgpc_ctx_create(ctypes.byref(h), 0) < 0
+
+
+def test_struct_layout_against_the_c_compiler(tmp_path):
+    """sizeof / offsetof of every ABI struct, from gcc on include/bgpc.h,
+    equal the ctypes mirrors of the binding."""
+    import subprocess
+    import paper_1701_02628_gb300 as bg
+    fields = {"bgpc_graph_t": ["n_a", "n_b", "nnz", "a_ptr", "a_idx", "b_ptr", "b_idx"],
+              "bgpc_ugraph_t": ["n", "nnz", "ptr", "idx"],
+              "bgpc_opts_t": [f for f, _ in bg.bgpc_opts_t._fields_],
+              "bgpc_stats_t": [f for f, _ in bg.bgpc_stats_t._fields_],
+              "bgpc_mlp_t": ["w", "w_bf16", "adam_m", "adam_v", "step"]}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', f'#include "{HEADER}"',
+             "int main(void) {"]
+    for st, fs in fields.items():
+        lines.append(f'  printf("{st} size %zu\\n", sizeof({st}));')
+        for f in fs:
+            lines.append(f'  printf("{st} {f} %zu\\n", offsetof({st}, {f}));')
+    lines.append("  return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-std=c11", "-o", str(exe), str(src)])
+    got = {}
+    for line in subprocess.check_output([str(exe)], text=True).splitlines():
+        st, f, v = line.split()
+        got[(st, f)] = int(v)
+    for st in fields:
+        cls = getattr(bg, st)
+        assert got[(st, "size")] == ctypes.sizeof(cls), st
+        for f in fields[st]:
+            assert got[(st, f)] == getattr(cls, f).offset, (st, f)
