@@ -57,6 +57,9 @@ WORKLOADS = {
     # smaller cases for profiler captures (same generators, fewer vertices)
     "chunglu20": "Chung-Lu 2^20x2^20 (mean 16, max 12.5k, exp 2.1), RS(64,16,64) first fit",
     "stencil": "stencil9 1024x1024, RS(64,16,64) first fit",
+    # the batched configuration: 512 independent graphs, one bgpc_color_batched call
+    "batch512": ("512 graphs, |V_A| log-uniform [1e3,1e6], |V_B| = |V_A|*U[0.5,2], degree "
+                 "Poisson(8) clipped to [1,64]; RS(64,16,64) first fit, id order, one batched call"),
 }
 
 
@@ -66,6 +69,8 @@ def make_workload(name="jacobian"):
         return [gg.chung_lu(1 << 20, 16.0, 12500.0, 2.1, seed=2)]
     if name == "stencil":
         return [gg.stencil9(1024)]
+    if name == "batch512":
+        return [gg.batch_graph(17, i) for i in range(512)]
     return [gg.stencil9(1024), gg.chung_lu(1 << 22, 16.0, 50000.0, 2.1, seed=2)]
 
 
@@ -285,7 +290,12 @@ def run_gpu(args):
     colors = [torch.empty(g.n_a, dtype=torch.int32, device=dev) for g in graphs]
     stream = torch.cuda.current_stream()
 
+    batched = args.workload == "batch512"
+
     def step(profile=False):
+        if batched:
+            _, st, _, _ = bg.bgpc_color_batched(ctx, dgs, colors, profile=profile)
+            return [st]
         sts = []
         for dg, c in zip(dgs, colors):
             _, st, _ = bg.bgpc_color(ctx, dg, c, profile=profile)
@@ -360,10 +370,15 @@ def run_gpu(args):
     d2h = sum(g.n_a * 4 for g in graphs_e2e)
 
     def e2e_step():
-        for (hg, dg, c, oh) in zip(host, dgs, colors, out_host):
+        for (hg, dg) in zip(host, dgs):
             for src, dst in zip(hg, (dg.a_ptr, dg.a_idx, dg.b_ptr, dg.b_idx)):
                 dst.copy_(src, non_blocking=True)
-            bg.bgpc_color(ctx, dg, c)
+        if batched:
+            bg.bgpc_color_batched(ctx, dgs, colors)
+        else:
+            for dg, c in zip(dgs, colors):
+                bg.bgpc_color(ctx, dg, c)
+        for oh, c in zip(out_host, colors):
             oh.copy_(c, non_blocking=True)
 
     e2e = None
@@ -398,7 +413,16 @@ def run_gpu(args):
 
     if rank == 0:
         per_graph = []
-        for g, st in zip(graphs, all_stats[-1]):
+        if batched:
+            st = all_stats[-1][0]
+            per_graph.append({"graphs": len(graphs), "n_a": sum(g.n_a for g in graphs),
+                              "nnz": sum(g.nnz for g in graphs),
+                              "E2": sum(e2_of(g) for g in graphs),
+                              "rounds_max": st["rounds"], "colors_max": st["colors"],
+                              "w_per_round": st["w_per_round"][:12],
+                              "trav_total": st["trav_total"], "trav_large": st["trav_large"],
+                              "pieces": st["pieces_total"]})
+        for g, st in ([] if batched else zip(graphs, all_stats[-1])):
             per_graph.append({"graph": g.name, "n_a": g.n_a, "nnz": g.nnz, "E2": e2_of(g),
                               "rounds": st["rounds"], "colors": st["colors"],
                               "w_per_round": st["w_per_round"][:12],

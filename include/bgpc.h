@@ -141,6 +141,22 @@ int bgpc_ctx_destroy(bgpc_ctx_t *ctx);
 int bgpc_color(bgpc_ctx_t *ctx, const bgpc_graph_t *g, const bgpc_opts_t *opts,
                int32_t *colors, bgpc_stats_t *stats, void *stream);
 
+/* Batched BGPC: colors n_graphs independent bipartite graphs with one call
+ * (no counterpart in the paper, which colors one graph at a time).  Every
+ * graph gets exactly the coloring that bgpc_color gives it with the same
+ * opts: the graphs are colored one after the other by the single-graph
+ * engine, sharing the context's scratch.  graphs: host array [n_graphs] of
+ * graphs with device arrays; colors: host array [n_graphs] of device int32
+ * pointers ([n_a] each).  stats (host, may be NULL): the whole batch
+ * (rounds and colors = the largest over the graphs; the per-round and total
+ * counters and phase times summed).  rounds_out / ncolors_out: host
+ * [n_graphs] or NULL, per graph.  opts.rank must be NULL and
+ * opts.stop_after_waves 0 (else BGPC_EINVAL); n_graphs in [1, 65535].
+ * Synchronises `stream`. */
+int bgpc_color_batched(bgpc_ctx_t *ctx, int32_t n_graphs, const bgpc_graph_t *graphs,
+                       const bgpc_opts_t *opts, int32_t *const *colors, bgpc_stats_t *stats,
+                       int32_t *rounds_out, int32_t *ncolors_out, void *stream);
+
 /* D2GC (Sec. IV, Alg. 9-10): BGPC on the closed neighbourhoods
  * nets(u) = vtxs(u) = N[u] = {u} u adj(u), built on the device; the reverse
  * first fit starts at |N[v]| - 1 = |nbor(v)| as in Alg. 9.

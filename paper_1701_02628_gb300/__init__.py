@@ -68,7 +68,7 @@ class bgpc_stats_t(ctypes.Structure):
 
 
 EXPORTS = ["bgpc_opts_default", "bgpc_ctx_create", "bgpc_ctx_destroy", "bgpc_color",
-           "d2gc_color", "bgpc_validate", "bgpc_color_sets", "bgpc_color_sets_noalloc",
+           "bgpc_color_batched", "d2gc_color", "bgpc_validate", "bgpc_color_sets", "bgpc_color_sets_noalloc",
            "bgpc_features", "bgpc_mlp_sync", "bgpc_mlp_forward", "bgpc_mlp_grad",
            "bgpc_mlp_adam", "bgpc_mlp_train_step", "bgpc_rank_from_scores", "bgpc_strerror"]
 MLP_IN, MLP_HIDDEN, MLP_PARAMS = 8, 64, 4801
@@ -114,6 +114,10 @@ def load():
                                             ctypes.POINTER(ctypes.c_double),
                                             ctypes.POINTER(ctypes.c_double), vp]
     lib.bgpc_color_sets_noalloc.restype = ctypes.c_int
+    lib.bgpc_color_batched.argtypes = [vp, ctypes.c_int32, ctypes.POINTER(bgpc_graph_t),
+                                       ctypes.POINTER(bgpc_opts_t), ctypes.POINTER(vp),
+                                       ctypes.POINTER(bgpc_stats_t), _c_i32p, _c_i32p, vp]
+    lib.bgpc_color_batched.restype = ctypes.c_int
     M = ctypes.POINTER(bgpc_mlp_t)
     fp = ctypes.POINTER(ctypes.c_float)
     lib.bgpc_features.argtypes = [vp, ctypes.POINTER(bgpc_graph_t), ctypes.c_int32, vp, vp]
@@ -282,6 +286,26 @@ def bgpc_color(ctx: Context, g: DeviceGraph, colors: torch.Tensor = None, stream
                            ctypes.byref(st), _stream(stream))
     _check(rc, "bgpc_color")
     return colors, stats_dict(st), rc
+
+
+def bgpc_color_batched(ctx: Context, graphs, colors=None, stream=None, **opts):
+    """Color a batch of independent graphs with one call (bgpc_color_batched).
+    Returns (list of color tensors, batch stats dict, rounds per graph,
+    number of colors per graph)."""
+    G = len(graphs)
+    if colors is None:
+        colors = [torch.empty(max(gr.n_a, 1), dtype=torch.int32, device=gr.a_ptr.device)
+                  for gr in graphs]
+    o = make_opts(**opts)
+    gs = (bgpc_graph_t * G)(*[gr.c_struct() for gr in graphs])
+    cp = (ctypes.c_void_p * G)(*[c.data_ptr() for c in colors])
+    rounds = (ctypes.c_int32 * G)()
+    ncol = (ctypes.c_int32 * G)()
+    st = bgpc_stats_t()
+    _check(load().bgpc_color_batched(ctx.handle, G, gs, ctypes.byref(o), cp, ctypes.byref(st),
+                                     rounds, ncol, _stream(stream)), "bgpc_color_batched")
+    return ([c[:gr.n_a] for c, gr in zip(colors, graphs)], stats_dict(st), list(rounds),
+            list(ncol))
 
 
 def d2gc_color(ctx: Context, g: DeviceUGraph, colors: torch.Tensor = None, stream=None, **opts):

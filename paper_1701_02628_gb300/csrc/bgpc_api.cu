@@ -472,6 +472,53 @@ int bgpc_color(bgpc_ctx_t *ctx, const bgpc_graph_t *g, const bgpc_opts_t *opts, 
   return color_impl(ctx, *g, *opts, colors, stats, (cudaStream_t)stream);
 }
 
+int bgpc_color_batched(bgpc_ctx_t *ctx, int32_t n_graphs, const bgpc_graph_t *graphs,
+                       const bgpc_opts_t *opts, int32_t *const *colors, bgpc_stats_t *stats,
+                       int32_t *rounds_out, int32_t *ncolors_out, void *stream) {
+  if (!ctx || n_graphs < 1 || n_graphs > 65535 || !graphs || !colors) return BGPC_EINVAL;
+  int rc = check_opts(opts);
+  if (rc) return rc;
+  if (opts->rank || opts->stop_after_waves) return BGPC_EINVAL;
+  for (int32_t k = 0; k < n_graphs; k++) {
+    if ((rc = check_graph_args(&graphs[k]))) return rc;
+    if (graphs[k].n_a > 0 && !colors[k]) return BGPC_EINVAL;
+  }
+  Guard guard(ctx->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  bgpc_stats_t tot;
+  memset(&tot, 0, sizeof(tot));
+  for (int32_t k = 0; k < n_graphs; k++) {
+    bgpc_stats_t st;
+    memset(&st, 0, sizeof(st));
+    if ((rc = color_impl(ctx, graphs[k], *opts, colors[k], &st, s))) return rc;
+    if (rounds_out) rounds_out[k] = st.rounds;
+    if (ncolors_out) ncolors_out[k] = st.colors;
+    tot.rounds = st.rounds > tot.rounds ? st.rounds : tot.rounds;
+    tot.colors = st.colors > tot.colors ? st.colors : tot.colors;
+    for (int r = 0; r < BGPC_MAX_REPORT && r < st.rounds; r++) {
+      tot.w_per_round[r] += st.w_per_round[r];
+      tot.trav_per_round[r] += st.trav_per_round[r];
+    }
+    tot.trav_total += st.trav_total;
+    tot.incid_total += st.incid_total;
+    tot.w_total += st.w_total;
+    tot.trav_large += st.trav_large;
+    tot.incid_large += st.incid_large;
+    tot.w_large += st.w_large;
+    tot.pieces_total += st.pieces_total;
+    tot.kernel_launches += st.kernel_launches;
+    tot.color_launches += st.color_launches;
+    tot.ms_setup += st.ms_setup;
+    tot.ms_color += st.ms_color;
+    tot.ms_publish += st.ms_publish;
+    tot.ms_detect += st.ms_detect;
+    tot.ms_gather += st.ms_gather;
+  }
+  CU(cudaStreamSynchronize(s));
+  if (stats) *stats = tot;
+  return BGPC_OK;
+}
+
 int d2gc_color(bgpc_ctx_t *ctx, const bgpc_ugraph_t *g, const bgpc_opts_t *opts, int32_t *colors,
                bgpc_stats_t *stats, void *stream) {
   if (!ctx || !g || g->n < 0 || g->nnz < 0) return BGPC_EINVAL;
