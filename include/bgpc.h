@@ -100,7 +100,9 @@ typedef struct {
                                 of a round, stop before its conflict removal
                                 (colors = every vertex's tentative color,
                                 stopped_wave = waves) */
-    int32_t reserved[5];
+    int32_t batch_streams;   /* bgpc_color_batched only: graphs colored concurrently
+                                (0 = 8); a mapping parameter, results do not change */
+    int32_t reserved[4];
 } bgpc_opts_t;
 
 /* Statistics of one call (host struct). */

@@ -47,7 +47,7 @@ class bgpc_opts_t(ctypes.Structure):
                 ("validate", ctypes.c_int32), ("stop_after_waves", ctypes.c_int64),
                 ("W_out", ctypes.c_void_p), ("want_balance", ctypes.c_int32),
                 ("profile", ctypes.c_int32), ("stop_before_removal", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 5)]
+                ("batch_streams", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
 
 
 class bgpc_stats_t(ctypes.Structure):
@@ -247,7 +247,7 @@ def bgpc_opts_default() -> bgpc_opts_t:
 
 def make_opts(policy=BGPC_FF, chunk=64, waves=16, big_net=64, rank=None, max_rounds=1000,
               validate=False, stop_after_waves=0, W_out=None, want_balance=False,
-              profile=False, stop_before_removal=False) -> bgpc_opts_t:
+              profile=False, stop_before_removal=False, batch_streams=0) -> bgpc_opts_t:
     o = bgpc_opts_default()
     o.policy, o.chunk, o.waves, o.big_net = policy, chunk, waves, big_net
     o.rank = _ptr(rank)
@@ -258,6 +258,7 @@ def make_opts(policy=BGPC_FF, chunk=64, waves=16, big_net=64, rank=None, max_rou
     o.want_balance = int(bool(want_balance))
     o.profile = int(bool(profile))
     o.stop_before_removal = int(bool(stop_before_removal))
+    o.batch_streams = batch_streams
     return o
 
 

@@ -4,6 +4,10 @@
 #include <math.h>
 #include <string.h>
 
+#include <atomic>
+#include <thread>
+#include <vector>
+
 #include "bgpc_internal.cuh"
 
 using namespace bgpc;
@@ -450,6 +454,10 @@ int bgpc_ctx_destroy(bgpc_ctx_t *ctx) {
   release(ctx->wlist); release(ctx->segoff); release(ctx->segmap); release(ctx->gbm);
   release(ctx->gadj);
   if (ctx->h_wlist) cudaFreeHost(ctx->h_wlist);
+  for (bgpc_ctx_t *sub : ctx->subs) bgpc_ctx_destroy(sub);
+  for (cudaStream_t st : ctx->sub_streams) cudaStreamDestroy(st);
+  ctx->subs.clear();
+  ctx->sub_streams.clear();
   release(ctx->card); release(ctx->bad);
   release(ctx->rkey0); release(ctx->rkey1); release(ctx->rval0); release(ctx->rval1);
   release(ctx->rhist); release(ctx->rsum); release(ctx->mpart); release(ctx->mgrad);
@@ -478,19 +486,68 @@ int bgpc_color_batched(bgpc_ctx_t *ctx, int32_t n_graphs, const bgpc_graph_t *gr
   if (!ctx || n_graphs < 1 || n_graphs > 65535 || !graphs || !colors) return BGPC_EINVAL;
   int rc = check_opts(opts);
   if (rc) return rc;
-  if (opts->rank || opts->stop_after_waves) return BGPC_EINVAL;
+  if (opts->rank || opts->stop_after_waves || opts->batch_streams < 0 ||
+      opts->batch_streams > 64)
+    return BGPC_EINVAL;
   for (int32_t k = 0; k < n_graphs; k++) {
     if ((rc = check_graph_args(&graphs[k]))) return rc;
     if (graphs[k].n_a > 0 && !colors[k]) return BGPC_EINVAL;
   }
   Guard guard(ctx->device);
   cudaStream_t s = (cudaStream_t)stream;
+  int K = opts->batch_streams > 0 ? opts->batch_streams : 8;
+  if (K > n_graphs) K = n_graphs;
+  while ((int)ctx->subs.size() < K) {
+    bgpc_ctx_t *sub = nullptr;
+    if ((rc = bgpc_ctx_create(&sub, ctx->device))) return rc;
+    cudaStream_t st = nullptr;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError();
+      bgpc_ctx_destroy(sub);
+      return BGPC_ECUDA;
+    }
+    ctx->subs.push_back(sub);
+    ctx->sub_streams.push_back(st);
+  }
+  // the workers' streams start after everything already queued on `stream`
+  cudaEvent_t ev = nullptr;
+  CU(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+  CU(cudaEventRecord(ev, s));
+  for (int w = 0; w < K; w++) CU(cudaStreamWaitEvent(ctx->sub_streams[(size_t)w], ev, 0));
+  std::vector<bgpc_stats_t> per((size_t)n_graphs);
+  std::atomic<int32_t> next(0);
+  std::atomic<int> err(0);
+  auto work = [&](int w) {
+    cudaSetDevice(ctx->device);
+    for (;;) {
+      if (err.load() != 0) return;
+      const int32_t k = next.fetch_add(1);
+      if (k >= n_graphs) return;
+      memset(&per[(size_t)k], 0, sizeof(bgpc_stats_t));
+      const int r = color_impl(ctx->subs[(size_t)w], graphs[k], *opts, colors[k],
+                               &per[(size_t)k], ctx->sub_streams[(size_t)w]);
+      if (r != BGPC_OK) {
+        int zero = 0;
+        err.compare_exchange_strong(zero, r);
+        return;
+      }
+    }
+  };
+  if (K == 1) {
+    work(0);
+  } else {
+    std::vector<std::thread> th;
+    th.reserve((size_t)K);
+    for (int w = 0; w < K; w++) th.emplace_back(work, w);
+    for (auto &t : th) t.join();
+  }
+  for (int w = 0; w < K; w++) cudaStreamSynchronize(ctx->sub_streams[(size_t)w]);
+  cudaEventDestroy(ev);
+  if (err.load() != 0) return err.load();
   bgpc_stats_t tot;
   memset(&tot, 0, sizeof(tot));
   for (int32_t k = 0; k < n_graphs; k++) {
-    bgpc_stats_t st;
-    memset(&st, 0, sizeof(st));
-    if ((rc = color_impl(ctx, graphs[k], *opts, colors[k], &st, s))) return rc;
+    const bgpc_stats_t &st = per[(size_t)k];
     if (rounds_out) rounds_out[k] = st.rounds;
     if (ncolors_out) ncolors_out[k] = st.colors;
     tot.rounds = st.rounds > tot.rounds ? st.rounds : tot.rounds;
@@ -514,7 +571,6 @@ int bgpc_color_batched(bgpc_ctx_t *ctx, int32_t n_graphs, const bgpc_graph_t *gr
     tot.ms_detect += st.ms_detect;
     tot.ms_gather += st.ms_gather;
   }
-  CU(cudaStreamSynchronize(s));
   if (stats) *stats = tot;
   return BGPC_OK;
 }

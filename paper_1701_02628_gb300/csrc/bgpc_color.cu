@@ -955,12 +955,28 @@ __global__ void k_publish(const int32_t *__restrict__ a_ptr, const int32_t *__re
 constexpr int kWaveNT = 256;
 constexpr int kGatherNT = 256;
 
+// Lets the kernel take all the dynamic shared memory the device allows next to
+// its static arrays.  Always the same value, so concurrent callers (the
+// batched entry point colors graphs from several host threads) never see a
+// smaller limit than the one they launch with.
+template <typename K>
+cudaError_t allow_dynamic_smem(K kern) {
+  int dev = 0, optin = 0;
+  cudaFuncAttributes fa;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess)
+    e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, kern);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              optin - (int)fa.sharedSizeBytes);
+}
+
 template <int POLICY>
 cudaError_t launch_policy(const WaveArgs &a, int sms, cudaStream_t s) {
   auto kern = k_color_wave<POLICY, kWaveNT>;
   const size_t smem = (size_t)a.words * 4;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
+  cudaError_t e = allow_dynamic_smem(kern);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kWaveNT, smem);
@@ -999,8 +1015,7 @@ cudaError_t launch_gather(const GatherArgs &a, int sms, cudaStream_t s) {
   if (a.slot_hi <= a.slot_lo) return cudaSuccess;
   auto kern = k_gather<kGatherNT>;
   const size_t smem = (size_t)a.words * 4;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
+  cudaError_t e = allow_dynamic_smem(kern);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kGatherNT, smem);

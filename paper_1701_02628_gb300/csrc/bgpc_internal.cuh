@@ -67,6 +67,10 @@ struct Buf {
 
 struct bgpc_ctx {
   int device = 0;
+  // bgpc_color_batched: one sub-context (own scratch) and one stream per
+  // concurrent worker, created on first use and kept with the context
+  std::vector<bgpc_ctx *> subs;
+  std::vector<cudaStream_t> sub_streams;
   int num_sms = 0;
   int smem_optin = 0;  // max dynamic shared memory per block (bytes)
   bgpc::Buf<int32_t> tpos, nc, npos;

@@ -78,3 +78,21 @@ def test_batched_rejects_bad_arguments(bg, ctx):
     # the same graph twice is fine: the batch copies it side by side
     cols, _, _, _ = bg.bgpc_color_batched(ctx, [g, g])
     assert torch.equal(cols[0], cols[1])
+
+
+def test_batch_streams_is_a_mapping_parameter(bg, ctx):
+    graphs = [gg.batch_graph(5, i, lo=1e3, hi=3e4) for i in range(20)]
+    dgs = [bg.DeviceGraph.from_host(g, "cuda:0") for g in graphs]
+    ref = None
+    for k in (1, 3, 8, 16):
+        cols, st, rounds, ncol = bg.bgpc_color_batched(ctx, dgs, batch_streams=k)
+        got = [c.cpu().numpy() for c in cols]
+        if ref is None:
+            ref = (got, rounds, ncol, st["trav_total"])
+            for g, c in zip(graphs[:4], got):
+                assert np.array_equal(c, O.rs_color(g).colors)
+        else:
+            assert all(np.array_equal(a, b) for a, b in zip(got, ref[0]))
+            assert (rounds, ncol, st["trav_total"]) == ref[1:]
+    with pytest.raises(bg.BgpcError):
+        bg.bgpc_color_batched(ctx, dgs, batch_streams=-1)
