@@ -56,6 +56,7 @@ WORKLOADS = {
     "jacobian": WORKLOAD,
     # smaller cases for profiler captures (same generators, fewer vertices)
     "chunglu20": "Chung-Lu 2^20x2^20 (mean 16, max 12.5k, exp 2.1), RS(64,16,64) first fit",
+    "chunglu22": "Chung-Lu 2^22x2^22 (mean 16, max 50k, exp 2.1), RS(64,16,64) first fit",
     "stencil": "stencil9 1024x1024, RS(64,16,64) first fit",
     # the batched configuration: 512 independent graphs, one bgpc_color_batched call
     "batch512": ("512 graphs, |V_A| log-uniform [1e3,1e6], |V_B| = |V_A|*U[0.5,2], degree "
@@ -69,6 +70,8 @@ def make_workload(name="jacobian"):
         return [gg.chung_lu(1 << 20, 16.0, 12500.0, 2.1, seed=2)]
     if name == "stencil":
         return [gg.stencil9(1024)]
+    if name == "chunglu22":
+        return [gg.chung_lu(1 << 22, 16.0, 50000.0, 2.1, seed=2)]
     if name == "batch512":
         return [gg.batch_graph(17, i) for i in range(512)]
     return [gg.stencil9(1024), gg.chung_lu(1 << 22, 16.0, 50000.0, 2.1, seed=2)]
@@ -333,15 +336,17 @@ def run_gpu(args):
 
     # roofline of the dominant kernel: algorithmic bytes per launch / mean
     # launch duration, both over the timed region.  The gather kernel streams
-    # the mirror entries of the vertices that take the multi-CTA path, the
-    # resolve kernel those of the small vertices (4 B per streamed entry, 12 B
-    # per incidence for a_idx and the b_ptr pair, 28 B per small vertex).
+    # the mirror entries of the large vertices' nets except the hub nets
+    # (4 B per entry), reads a hub net's color bitmap instead (4 B per word),
+    # plus 12 B per incidence (a_idx and the b_ptr pair); the resolve kernel
+    # streams the small vertices' entries, plus 28 B per small vertex.
     def tot(key):
         return sum(st[key] for sts in all_stats for st in sts)
     n_launch = tot("color_launches")
     kern = {
         "k_gather": (tot("ms_gather"),
-                     4 * (tot("trav_large") + tot("incid_large")) + 12 * tot("incid_large")),
+                     4 * (tot("trav_large") - tot("trav_hub") + tot("incid_large"))
+                     + 12 * tot("incid_large") + 4 * tot("hub_words")),
         "k_color_wave": (tot("ms_color"),
                          4 * (tot("trav_total") - tot("trav_large") + tot("incid_total")
                               - tot("incid_large")) + 12 * (tot("incid_total") - tot("incid_large"))
@@ -427,7 +432,9 @@ def run_gpu(args):
                               "rounds": st["rounds"], "colors": st["colors"],
                               "w_per_round": st["w_per_round"][:12],
                               "trav_total": st["trav_total"],
-                              "trav_large": st["trav_large"], "pieces": st["pieces_total"]})
+                              "trav_large": st["trav_large"], "pieces": st["pieces_total"],
+                              "trav_hub": st["trav_hub"], "hub_pairs": st["hub_pairs"],
+                              "hub_words": st["hub_words"]})
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,

@@ -125,6 +125,10 @@ typedef struct {
     int64_t kernel_launches;              /* kernels this call launched */
     int64_t color_launches;               /* wave-coloring kernel launches */
     double ms_setup, ms_color, ms_publish, ms_detect, ms_gather; /* device time per phase (profile) */
+    int64_t trav_hub;    /* all rounds: the part of trav_large in hub nets (more than 1024
+                            members), read from per-net color bitmaps instead of streamed */
+    int64_t hub_pairs;   /* all rounds: (vertex, hub net) pairs so read */
+    int64_t hub_words;   /* all rounds: bitmap words so read (hub_pairs x the round's width) */
 } bgpc_stats_t;
 
 /* Fill `opts` with the defaults: FF, C=64, Q=16, T=64, id order,

@@ -64,7 +64,8 @@ class bgpc_stats_t(ctypes.Structure):
                 ("kernel_launches", ctypes.c_int64), ("color_launches", ctypes.c_int64),
                 ("ms_setup", ctypes.c_double), ("ms_color", ctypes.c_double),
                 ("ms_publish", ctypes.c_double), ("ms_detect", ctypes.c_double),
-                ("ms_gather", ctypes.c_double)]
+                ("ms_gather", ctypes.c_double), ("trav_hub", ctypes.c_int64),
+                ("hub_pairs", ctypes.c_int64), ("hub_words", ctypes.c_int64)]
 
 
 EXPORTS = ["bgpc_opts_default", "bgpc_ctx_create", "bgpc_ctx_destroy", "bgpc_color",
@@ -273,7 +274,8 @@ def stats_dict(st: bgpc_stats_t) -> dict:
                 pieces_total=st.pieces_total,
                 kernel_launches=st.kernel_launches,
                 color_launches=st.color_launches, ms_setup=st.ms_setup, ms_color=st.ms_color,
-                ms_publish=st.ms_publish, ms_detect=st.ms_detect, ms_gather=st.ms_gather)
+                ms_publish=st.ms_publish, ms_detect=st.ms_detect, ms_gather=st.ms_gather,
+                trav_hub=st.trav_hub, hub_pairs=st.hub_pairs, hub_words=st.hub_words)
 
 
 def bgpc_color(ctx: Context, g: DeviceGraph, colors: torch.Tensor = None, stream=None, **opts):

@@ -170,6 +170,8 @@ int color_impl(bgpc_ctx_t *ctx, const bgpc_graph_t &g, const bgpc_opts_t &o, int
   CU(grow(ctx->segmap, (size_t)n_a + (size_t)nnz / kPiece + 16));
   CU(grow(ctx->bigt, (size_t)(n_b > 0 ? n_b : 1)));
   CU(grow(ctx->bigd, (size_t)(n_b > 0 ? n_b : 1)));
+  CU(grow(ctx->hub_id, (size_t)(n_b > 0 ? n_b : 1)));
+  CU(grow(ctx->hub_net, (size_t)nnz / (kHubMin + 1) + 1));
 
   // ---- setup (Alg. 1: W <- V_color, c <- -1), static graph analysis
   PhaseTimer tm(ctx, s, o.profile != 0);
@@ -181,6 +183,7 @@ int color_impl(bgpc_ctx_t *ctx, const bgpc_graph_t &g, const bgpc_opts_t &o, int
   nk += launch_tpos(g, ctx->tpos.p, &ctx->dev->err, sms, s);
   nk += launch_vertex_static(g, ctx->tpos.p, ctx->s_own.p, ctx->d2tot.p, ctx->nown.p, sms, s);
   nk += launch_net_static(g, o.big_net, ctx->bigt.p, ctx->bigd.p, ctx->dev, s);
+  nk += launch_hub_select(g.b_ptr, n_b, kHubMin, ctx->hub_id.p, ctx->hub_net.p, ctx->dev, sms, s);
   nk += launch_init_queue(o.rank, n_a, ctx->W0.p, &ctx->dev->err, s);
   nk += launch_init_mirror(g, o.rank, ctx->tpos.p, ctx->nc.p, ctx->npos.p, colors, sms, s);
   tm.end(ev, PH_SETUP);
@@ -189,6 +192,7 @@ int color_impl(bgpc_ctx_t *ctx, const bgpc_graph_t &g, const bgpc_opts_t &o, int
   tm.collect();
   if (ctx->host->err) return err_to_status(ctx->host->err);
   const int32_t nbig_t = ctx->host->nbig_t, nbig_d = ctx->host->nbig_d;
+  const int32_t nhub = ctx->host->nhub;
   const int32_t maxnet = ctx->host->maxnet;
   const int32_t max_words = wave_max_words(ctx->smem_optin);
 
@@ -214,7 +218,7 @@ int color_impl(bgpc_ctx_t *ctx, const bgpc_graph_t &g, const bgpc_opts_t &o, int
     if (nbig_t > 0)
       nk += launch_kofs(g.b_ptr, ctx->nc.p, ctx->npos.p, ctx->nown.p, ctx->bigt.p, nbig_t,
                         ctx->kofs.p, sms, s);
-    CU(cudaMemsetAsync(&ctx->dev->trav, 0, 5 * sizeof(unsigned long long), s));
+    CU(cudaMemsetAsync(&ctx->dev->trav, 0, kRoundCounters * sizeof(unsigned long long), s));
     nk += launch_trav(g.a_ptr, W, ctx->d2tot.p, m, small_ok, ctx->dev, s);
     tm.end(ev, PH_DETECT);
 
@@ -251,7 +255,10 @@ int color_impl(bgpc_ctx_t *ctx, const bgpc_graph_t &g, const bgpc_opts_t &o, int
         ctx->gbm_zeroed = ctx->gbm.cap;
       }
     }
+    // the colors published so far, per hub net, at this round's bitmap width
+    if (nhub > 0) CU(grow(ctx->nbm, (size_t)nhub * (size_t)words));
     ev = tm.begin();
+    nk += launch_hub_build(g.b_ptr, ctx->nc.p, ctx->hub_net.p, nhub, words, ctx->nbm.p, sms, s);
     nk += launch_pieces(g.a_ptr, ctx->d2tot.p, W, ctx->wlist.p, (int32_t)nch, C, m, small_ok,
                         ctx->segoff.p, ctx->blocksum.p, ctx->segmap.p, ctx->dev, s);
     tm.end(ev, PH_DETECT);
@@ -287,6 +294,10 @@ int color_impl(bgpc_ctx_t *ctx, const bgpc_graph_t &g, const bgpc_opts_t &o, int
         ga.words = words;
         ga.gbm = ctx->gbm.p;
         ga.gadj = ctx->gadj.p;
+        ga.b_idx = g.b_idx;
+        ga.hub_id = nhub > 0 ? ctx->hub_id.p : nullptr;
+        ga.nbm = ctx->nbm.p;
+        ga.dev = ctx->dev;
         ev = tm.begin();
         CU(launch_gather(ga, sms, s));
         tm.end(ev, PH_GATHER);
@@ -319,8 +330,9 @@ int color_impl(bgpc_ctx_t *ctx, const bgpc_graph_t &g, const bgpc_opts_t &o, int
         nk++;
         st.color_launches++;
         ev = tm.begin();
-        nk += launch_publish(g.a_ptr, ctx->tpos.p, W, ctx->stage.p, wchunks, nwave, C, m,
-                             ctx->nc.p, colors, ctx->dev, sms, s);
+        nk += launch_publish(g.a_ptr, g.a_idx, ctx->tpos.p, W, ctx->stage.p, wchunks, nwave, C,
+                             m, ctx->nc.p, colors, nhub > 0 ? ctx->hub_id.p : nullptr,
+                             ctx->nbm.p, words, ctx->dev, sms, s);
         tm.end(ev, PH_PUBLISH);
       }
       waves_done++;
@@ -361,6 +373,9 @@ int color_impl(bgpc_ctx_t *ctx, const bgpc_graph_t &g, const bgpc_opts_t &o, int
     st.trav_large += (int64_t)ctx->host->trav_large;
     st.incid_large += (int64_t)ctx->host->incid_large;
     st.w_large += (int64_t)ctx->host->w_large;
+    st.trav_hub += (int64_t)ctx->host->trav_hub;
+    st.hub_pairs += (int64_t)ctx->host->hub_pairs;
+    st.hub_words += (int64_t)ctx->host->hub_pairs * words;
     st.pieces_total += ctx->host->nseg;
     st.w_total += m;
     r++;
@@ -450,6 +465,7 @@ int bgpc_ctx_destroy(bgpc_ctx_t *ctx) {
   release(ctx->s_own); release(ctx->d2tot); release(ctx->W0); release(ctx->W1);
   release(ctx->kofs); release(ctx->stage); release(ctx->newpos); release(ctx->lose);
   release(ctx->blocksum); release(ctx->bigt); release(ctx->bigd);
+  release(ctx->hub_id); release(ctx->hub_net); release(ctx->nbm);
   release(ctx->cptr); release(ctx->cidx); release(ctx->dtab); release(ctx->vtab);
   release(ctx->wlist); release(ctx->segoff); release(ctx->segmap); release(ctx->gbm);
   release(ctx->gadj);
@@ -562,6 +578,9 @@ int bgpc_color_batched(bgpc_ctx_t *ctx, int32_t n_graphs, const bgpc_graph_t *gr
     tot.trav_large += st.trav_large;
     tot.incid_large += st.incid_large;
     tot.w_large += st.w_large;
+    tot.trav_hub += st.trav_hub;
+    tot.hub_pairs += st.hub_pairs;
+    tot.hub_words += st.hub_words;
     tot.pieces_total += st.pieces_total;
     tot.kernel_launches += st.kernel_launches;
     tot.color_launches += st.color_launches;

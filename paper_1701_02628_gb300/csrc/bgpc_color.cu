@@ -707,6 +707,13 @@ __global__ void __launch_bounds__(NT) k_color_wave(WaveArgs a) {
 // equal contiguous slice of the piece's entries (net sizes differ by orders
 // of magnitude, so one warp per net would leave most warps waiting) and
 // streams it with 16-byte loads.
+//
+// Hub nets (more than kHubMin members) are not streamed: their published
+// colors are kept as one bitmap per net (built at the start of the round,
+// extended by every publish), so a member ORs `words` bitmap words instead of
+// reading |vtxs(v)| mirror entries, and finds its earlier chunk-mates in the
+// net by binary search of their ids in vtxs(v).  On power-law graphs the few
+// hub nets carry almost all of the two-hop volume (sum over nets of s^2).
 
 // One mirror word: a published color joins the forbidden bitmap; an earlier
 // chunk-mate (queue position in [p0, p0 + rel_hi)) joins the adjacency mask.
@@ -751,13 +758,24 @@ __device__ __forceinline__ void warp_stream(const int32_t *__restrict__ src, int
   if (t0 + lane < n) take(__ldg(src + t0 + lane), s_bm, lim, p0, rel_hi, adj);
 }
 
+// Whether vertex u is in the sorted list l[0, n).
+__device__ __forceinline__ bool sorted_has(const int32_t *__restrict__ l, int32_t n, int32_t u) {
+  int32_t lo = 0, hi = n;
+  while (lo < hi) {
+    const int32_t mid = (lo + hi) >> 1;
+    if (__ldg(l + mid) < u) lo = mid + 1; else hi = mid;
+  }
+  return lo < n && __ldg(l + lo) == u;
+}
+
 template <int NT>
 __global__ void __launch_bounds__(NT) k_gather(GatherArgs a) {
   constexpr int NW = NT / 32;
   extern __shared__ __align__(16) uint32_t s_bm[];
   __shared__ int32_t s_pstart[kPiece];
   __shared__ int32_t s_poff[kPiece + 1];
-  __shared__ int32_t s_info[4];  // p0, rel_hi, whole, nnets
+  __shared__ int32_t s_hslot[kPiece], s_hbp[kPiece], s_hsz[kPiece];  // hub nets of the piece
+  __shared__ int32_t s_info[5];  // p0, rel_hi, whole, nnets, hubs
   __shared__ int64_t s_slot;
   __shared__ unsigned long long s_adj;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -776,16 +794,32 @@ __global__ void __launch_bounds__(NT) k_gather(GatherArgs a) {
       const int32_t w = a.W[p];
       const int32_t ibeg = a.a_ptr[w] + piece * kPiece;
       const int32_t nnets = min(a.a_ptr[w + 1] - ibeg, kPiece);
-      int32_t sz = 0, bp = 0;
+      int32_t sz = 0, bp = 0, hub = -1;
       if (lane < nnets) {
         const int32_t v = a.a_idx[ibeg + lane];
         bp = a.b_ptr[v];
         sz = a.b_ptr[v + 1] - bp;
+        hub = a.hub_id ? a.hub_id[v] : -1;
       }
-      const int32_t inc = warp_incl_scan(sz);
+      // hub nets are read from their bitmaps; the others are streamed
+      const unsigned hubs = __ballot_sync(kFull, hub >= 0);
+      if (hub >= 0) {
+        const int32_t k = __popc(hubs & ((1u << lane) - 1u));
+        s_hslot[k] = hub;
+        s_hbp[k] = bp;
+        s_hsz[k] = sz;
+      }
+      const int32_t inc = warp_incl_scan(hub >= 0 ? 0 : sz);
       if (lane < kPiece) {
         s_pstart[lane] = bp;
         s_poff[lane + 1] = inc;
+      }
+      if (hubs) {
+        const int32_t hv = __reduce_add_sync(kFull, hub >= 0 ? sz - 1 : 0);
+        if (lane == 0) {
+          atomicAdd(&a.dev->trav_hub, (unsigned long long)hv);
+          atomicAdd(&a.dev->hub_pairs, (unsigned long long)__popc(hubs));
+        }
       }
       if (lane == 0) {
         s_poff[0] = 0;
@@ -793,15 +827,34 @@ __global__ void __launch_bounds__(NT) k_gather(GatherArgs a) {
         s_info[1] = p - p0;
         s_info[2] = (a.segoff[u + 1] - a.segoff[u]) == 1;
         s_info[3] = nnets;
+        s_info[4] = __popc(hubs);
         s_slot = (int64_t)(u - a.slot_lo);
       }
     }
     __syncthreads();
-    const int32_t p0 = s_info[0], rel_hi = s_info[1], nnets = s_info[3];
+    const int32_t p0 = s_info[0], rel_hi = s_info[1], nnets = s_info[3], nh = s_info[4];
+    unsigned long long adj = 0ull;
+    if (nh > 0) {
+      // hub nets: OR their bitmaps (16 bytes per thread and step) ...
+      const int32_t W4 = a.words >> 2;
+      const uint4 *nb4 = reinterpret_cast<const uint4 *>(a.nbm);
+      for (int32_t t = tid; t < nh * W4; t += NT) {
+        const int32_t h = t / W4, x = t - h * W4;
+        const uint4 q = __ldg(nb4 + (int64_t)s_hslot[h] * W4 + x);
+        if (q.x) atomicOr(&s_bm[4 * x + 0], q.x);
+        if (q.y) atomicOr(&s_bm[4 * x + 1], q.y);
+        if (q.z) atomicOr(&s_bm[4 * x + 2], q.z);
+        if (q.w) atomicOr(&s_bm[4 * x + 3], q.w);
+      }
+      // ... and find the earlier chunk-mates that are members
+      for (int32_t t = tid; t < nh * rel_hi; t += NT) {
+        const int32_t h = t / rel_hi, j = t - h * rel_hi;
+        if (sorted_has(a.b_idx + s_hbp[h], s_hsz[h], a.W[p0 + j])) adj |= 1ull << j;
+      }
+    }
     const int32_t E = s_poff[nnets];
     const int32_t per = (E + NW - 1) / NW;
     const int32_t lo_e = min(E, warp * per), hi_e = min(E, lo_e + per);
-    unsigned long long adj = 0ull;
     if (lo_e < hi_e) {
       int32_t t = 0;  // first net of the slice: largest t with s_poff[t] <= lo_e
       for (int32_t step = 8; step > 0; step >>= 1)
@@ -928,11 +981,13 @@ __global__ void __launch_bounds__(kScanNT) k_piece_scatter(int32_t nslots,
 
 // Publish: colors of the wave's positions go to c[] and to every CSC entry
 // of their edges (nc), and the running max color is updated.
-__global__ void k_publish(const int32_t *__restrict__ a_ptr, const int32_t *__restrict__ tpos,
+__global__ void k_publish(const int32_t *__restrict__ a_ptr, const int32_t *__restrict__ a_idx,
+                          const int32_t *__restrict__ tpos,
                           const int32_t *__restrict__ W, const int32_t *__restrict__ stage,
                           const int32_t *__restrict__ chunks, int32_t nchunks, int32_t C,
                           int32_t m, int32_t *__restrict__ nc, int32_t *__restrict__ colors,
-                          DevScalars *dev) {
+                          const int32_t *__restrict__ hub_id, uint32_t *__restrict__ nbm,
+                          int32_t words, DevScalars *dev) {
   const int lane = threadIdx.x & 31;
   int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -943,7 +998,13 @@ __global__ void k_publish(const int32_t *__restrict__ a_ptr, const int32_t *__re
     if (p >= m) continue;
     const int32_t w = W[p], col = stage[p];
     const int32_t beg = a_ptr[w], end = a_ptr[w + 1];
-    for (int32_t i = beg + lane; i < end; i += 32) nc[tpos[i]] = col;
+    for (int32_t i = beg + lane; i < end; i += 32) {
+      nc[tpos[i]] = col;
+      if (hub_id) {  // the color joins the bitmap of every hub net of w
+        const int32_t h = hub_id[a_idx[i]];
+        if (h >= 0) atomicOr(&nbm[(int64_t)h * words + (col >> 5)], 1u << (col & 31));
+      }
+    }
     if (lane == 0) colors[w] = col;
     mx = max(mx, col);
   }
@@ -1039,16 +1100,75 @@ int launch_pieces(const int32_t *a_ptr, const int32_t *d2tot, const int32_t *W,
   return 3;
 }
 
-int launch_publish(const int32_t *a_ptr, const int32_t *tpos, const int32_t *W,
-                   const int32_t *stage, const int32_t *chunks, int32_t nchunks, int32_t C,
-                   int32_t m, int32_t *nc, int32_t *colors, DevScalars *dev, int sms,
-                   cudaStream_t s) {
+int launch_publish(const int32_t *a_ptr, const int32_t *a_idx, const int32_t *tpos,
+                   const int32_t *W, const int32_t *stage, const int32_t *chunks,
+                   int32_t nchunks, int32_t C, int32_t m, int32_t *nc, int32_t *colors,
+                   const int32_t *hub_id, uint32_t *nbm, int32_t words, DevScalars *dev,
+                   int sms, cudaStream_t s) {
   if (nchunks <= 0) return 0;
   long long warps = (long long)nchunks * C;
   long long grid = div_up(warps * 32, 256);
   if (grid > (long long)sms * 16) grid = (long long)sms * 16;
-  k_publish<<<(int)grid, 256, 0, s>>>(a_ptr, tpos, W, stage, chunks, nchunks, C, m, nc, colors,
-                                      dev);
+  k_publish<<<(int)grid, 256, 0, s>>>(a_ptr, a_idx, tpos, W, stage, chunks, nchunks, C, m, nc,
+                                      colors, hub_id, nbm, words, dev);
+  return 1;
+}
+
+// ---------------------------------------------------------- hub nets
+// Nets with more than H members get a slot (order of the slots is irrelevant).
+__global__ void k_hub_select(const int32_t *__restrict__ b_ptr, int32_t n_b, int32_t H,
+                             int32_t *__restrict__ hub_id, int32_t *__restrict__ hub_net,
+                             DevScalars *dev) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n_b;
+       v += (int64_t)gridDim.x * blockDim.x) {
+    int32_t h = -1;
+    if (b_ptr[v + 1] - b_ptr[v] > H) {
+      h = atomicAdd(&dev->nhub, 1);
+      hub_net[h] = (int32_t)v;
+    }
+    hub_id[v] = h;
+  }
+}
+
+// Bitmap of the published colors of each hub net (one CTA per net, the
+// bitmap assembled in shared memory, written out whole).
+__global__ void __launch_bounds__(256) k_hub_build(const int32_t *__restrict__ b_ptr,
+                                                   const int32_t *__restrict__ nc,
+                                                   const int32_t *__restrict__ hub_net,
+                                                   int32_t nhub, int32_t words,
+                                                   uint32_t *__restrict__ nbm) {
+  extern __shared__ __align__(16) uint32_t s_bm[];
+  const int32_t lim = words * 32;
+  for (int32_t h = blockIdx.x; h < nhub; h += gridDim.x) {
+    for (int32_t x = threadIdx.x; x < words; x += blockDim.x) s_bm[x] = 0u;
+    __syncthreads();
+    const int32_t v = hub_net[h];
+    for (int32_t f = b_ptr[v] + threadIdx.x; f < b_ptr[v + 1]; f += blockDim.x) {
+      const int32_t c = nc[f];
+      if (c >= 0 && c < lim) atomicOr(&s_bm[c >> 5], 1u << (c & 31));
+    }
+    __syncthreads();
+    for (int32_t x = threadIdx.x; x < words; x += blockDim.x)
+      nbm[(int64_t)h * words + x] = s_bm[x];
+    __syncthreads();
+  }
+}
+
+int launch_hub_select(const int32_t *b_ptr, int32_t n_b, int32_t H, int32_t *hub_id,
+                      int32_t *hub_net, DevScalars *dev, int sms, cudaStream_t s) {
+  if (n_b <= 0) return 0;
+  long long grid = div_up(n_b, 256);
+  if (grid > (long long)sms * 8) grid = (long long)sms * 8;
+  k_hub_select<<<(int)grid, 256, 0, s>>>(b_ptr, n_b, H, hub_id, hub_net, dev);
+  return 1;
+}
+
+int launch_hub_build(const int32_t *b_ptr, const int32_t *nc, const int32_t *hub_net,
+                     int32_t nhub, int32_t words, uint32_t *nbm, int sms, cudaStream_t s) {
+  if (nhub <= 0) return 0;
+  if (allow_dynamic_smem(k_hub_build) != cudaSuccess) return 0;  // reported by the caller
+  const int grid = nhub < sms * 4 ? nhub : sms * 4;
+  k_hub_build<<<grid, 256, (size_t)words * 4, s>>>(b_ptr, nc, hub_net, nhub, words, nbm);
   return 1;
 }
 

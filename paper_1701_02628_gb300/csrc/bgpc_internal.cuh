@@ -51,11 +51,18 @@ struct DevScalars {
   int32_t maxnet;    // largest net
   int32_t maxcolor;  // for validation / statistics
   int32_t nseg;      // gather pieces of the round
+  int32_t nhub;      // hub nets of the round (their colors kept as bitmaps)
+  int32_t pad;
   unsigned long long trav;   // traversed two-hop entries of the round
   unsigned long long incid;  // incidences sum over W_r of |nets(w)| of the round
   unsigned long long trav_large, incid_large, w_large;  // the same over gathered (large) vertices
+  unsigned long long trav_hub;   // two-hop entries of hub nets, read as bitmaps instead
+  unsigned long long hub_pairs;  // (vertex, hub net) pairs gathered from bitmaps
   unsigned long long acc[4]; // reductions (statistics)
 };
+constexpr int kRoundCounters = 7;  // trav .. hub_pairs, zeroed at the start of a round
+constexpr int32_t kHubMin = 1024;  // a hub net has more members than this and than the
+                                   // round's bitmap words
 
 template <typename T>
 struct Buf {
@@ -82,6 +89,8 @@ struct bgpc_ctx {
   bgpc::Buf<int32_t> segoff;           // gather pieces: exclusive prefix in wave order
   bgpc::Buf<int2> segmap;              // gather piece -> (wave-order slot, piece index)
   bgpc::Buf<uint32_t> gbm;             // per-slot forbidden bitmaps of large vertices
+  bgpc::Buf<int32_t> hub_id, hub_net;  // net -> hub slot (-1: not a hub), slot -> net
+  bgpc::Buf<uint32_t> nbm;             // hub color bitmaps [nhub][words]
   bgpc::Buf<unsigned long long> gadj;  // per-slot chunk-mate adjacency of large vertices
   size_t gbm_zeroed = 0;               // words of gbm known to be zero
   int32_t *h_wlist = nullptr;          // pinned host staging of wlist
@@ -176,6 +185,10 @@ struct GatherArgs {
   int32_t words;
   uint32_t *gbm;
   unsigned long long *gadj;
+  const int32_t *b_idx;        // vtxs lists (chunk-mate search in hub nets)
+  const int32_t *hub_id;       // net -> hub slot or -1
+  const uint32_t *nbm;         // hub color bitmaps [nhub][words] (the wave snapshot)
+  DevScalars *dev;             // hub counters
 };
 // Largest bitmap (in words) the wave kernels can hold in shared memory.
 int32_t wave_max_words(int smem_optin);
@@ -186,10 +199,17 @@ int launch_pieces(const int32_t *a_ptr, const int32_t *d2tot, const int32_t *W,
                   const int32_t *wlist, int32_t nch, int32_t C, int32_t m, int32_t small_ok,
                   int32_t *segoff, int32_t *blocksum, int2 *segmap, DevScalars *dev,
                   cudaStream_t s);
-int launch_publish(const int32_t *a_ptr, const int32_t *tpos, const int32_t *W,
-                   const int32_t *stage, const int32_t *chunks, int32_t nchunks, int32_t C,
-                   int32_t m, int32_t *nc, int32_t *colors, DevScalars *dev, int sms,
-                   cudaStream_t s);
+int launch_publish(const int32_t *a_ptr, const int32_t *a_idx, const int32_t *tpos,
+                   const int32_t *W, const int32_t *stage, const int32_t *chunks,
+                   int32_t nchunks, int32_t C, int32_t m, int32_t *nc, int32_t *colors,
+                   const int32_t *hub_id, uint32_t *nbm, int32_t words, DevScalars *dev,
+                   int sms, cudaStream_t s);
+// Per round: hub nets (more than H members) get a slot (hub_id, -1 otherwise)
+// and a color bitmap of their published members.
+int launch_hub_select(const int32_t *b_ptr, int32_t n_b, int32_t H, int32_t *hub_id,
+                      int32_t *hub_net, DevScalars *dev, int sms, cudaStream_t s);
+int launch_hub_build(const int32_t *b_ptr, const int32_t *nc, const int32_t *hub_net,
+                     int32_t nhub, int32_t words, uint32_t *nbm, int sms, cudaStream_t s);
 
 // Wave of chunk j under Q waves: the Weyl sequence frac(j * phi), phi =
 // 0x9E3779B9 / 2^32, scaled to [0, Q).

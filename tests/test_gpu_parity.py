@@ -80,6 +80,34 @@ def test_policies_power_law(bg, ctx, policy):
     assert_parity(bg, ctx, g, policy=policy)
 
 
+def hub_graph():
+    """Three nets above the hub threshold (1024 members), overlapping, plus
+    2500 small random nets: the members of a hub net gather it from its
+    color bitmap and find their chunk-mates in it by binary search."""
+    rng = np.random.default_rng(4)
+    nets = [list(range(0, 1500)), list(range(500, 3000)), list(rng.choice(3000, 1100, replace=False))]
+    nets += [list(rng.choice(3000, rng.integers(2, 40), replace=False)) for _ in range(2500)]
+    return gg.from_nets(3000, [sorted(set(int(x) for x in n)) for n in nets])
+
+
+@pytest.mark.parametrize("policy", POLICIES)
+def test_hub_nets(bg, ctx, policy):
+    g = hub_graph()
+    st = assert_parity(bg, ctx, g, policy=policy)
+    assert st["hub_pairs"] > 0 and st["trav_hub"] > 0
+    g = gg.chung_lu(30000, 12, 6000, 2.1, seed=3)  # 17 nets above 1024 members
+    st = assert_parity(bg, ctx, g, policy=policy)
+    assert st["hub_pairs"] > 0
+
+
+@pytest.mark.parametrize("policy", [O.FF, O.B2])
+def test_hub_nets_rank_and_small_chunks(bg, ctx, policy):
+    g = hub_graph()
+    rank = np.random.default_rng(9).permutation(g.n_a).astype(np.int32)
+    assert_parity(bg, ctx, g, policy=policy, rank=rank)
+    assert_parity(bg, ctx, g, policy=policy, chunk=5, waves=7, big_net=300)
+
+
 @pytest.mark.parametrize("chunk,waves,big_net", [(1, 1, O.NO_BIG), (7, 3, 2), (32, 16, 0),
                                                  (64, 1, 8), (64, 64, O.NO_BIG), (13, 5, 64)])
 def test_semantic_parameters(bg, ctx, chunk, waves, big_net):
