@@ -298,6 +298,7 @@ int color_impl(bgpc_ctx_t *ctx, const bgpc_graph_t &g, const bgpc_opts_t &o, int
         ga.hub_id = nhub > 0 ? ctx->hub_id.p : nullptr;
         ga.nbm = ctx->nbm.p;
         ga.dev = ctx->dev;
+        ga.id_order = o.rank ? 0 : 1;
         ev = tm.begin();
         CU(launch_gather(ga, sms, s));
         tm.end(ev, PH_GATHER);

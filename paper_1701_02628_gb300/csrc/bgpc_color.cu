@@ -758,13 +758,19 @@ __device__ __forceinline__ void warp_stream(const int32_t *__restrict__ src, int
   if (t0 + lane < n) take(__ldg(src + t0 + lane), s_bm, lim, p0, rel_hi, adj);
 }
 
-// Whether vertex u is in the sorted list l[0, n).
-__device__ __forceinline__ bool sorted_has(const int32_t *__restrict__ l, int32_t n, int32_t u) {
+// First index of the sorted list l[0, n) whose value is >= u.
+__device__ __forceinline__ int32_t lower_bound(const int32_t *__restrict__ l, int32_t n, int32_t u) {
   int32_t lo = 0, hi = n;
   while (lo < hi) {
     const int32_t mid = (lo + hi) >> 1;
     if (__ldg(l + mid) < u) lo = mid + 1; else hi = mid;
   }
+  return lo;
+}
+
+// Whether vertex u is in the sorted list l[0, n).
+__device__ __forceinline__ bool sorted_has(const int32_t *__restrict__ l, int32_t n, int32_t u) {
+  const int32_t lo = lower_bound(l, n, u);
   return lo < n && __ldg(l + lo) == u;
 }
 
@@ -847,9 +853,28 @@ __global__ void __launch_bounds__(NT) k_gather(GatherArgs a) {
         if (q.w) atomicOr(&s_bm[4 * x + 3], q.w);
       }
       // ... and find the earlier chunk-mates that are members
-      for (int32_t t = tid; t < nh * rel_hi; t += NT) {
-        const int32_t h = t / rel_hi, j = t - h * rel_hi;
-        if (sorted_has(a.b_idx + s_hbp[h], s_hsz[h], a.W[p0 + j])) adj |= 1ull << j;
+      if (a.id_order && rel_hi > 0) {
+        // the chunk's ids increase with the position: its earlier members
+        // lie between the ids of its first and last earlier vertex, a short
+        // stretch of vtxs(v) located by two binary searches (one warp per
+        // hub net), whose mirror words carry their queue positions
+        const int32_t id_lo = a.W[p0], id_hi = a.W[p0 + rel_hi - 1];
+        for (int32_t h = warp; h < nh; h += NW) {
+          const int32_t *l = a.b_idx + s_hbp[h];
+          int32_t b = 0;
+          if (lane < 2) b = lower_bound(l, s_hsz[h], lane == 0 ? id_lo : id_hi + 1);
+          const int32_t lb = __shfl_sync(kFull, b, 0), ub = __shfl_sync(kFull, b, 1);
+          for (int32_t f = lb + lane; f < ub; f += 32) {
+            const int32_t x = a.nc[s_hbp[h] + f];
+            const int32_t rel = (-2 - x) - p0;
+            if (x < 0 && rel >= 0 && rel < rel_hi) adj |= 1ull << rel;
+          }
+        }
+      } else {
+        for (int32_t t = tid; t < nh * rel_hi; t += NT) {
+          const int32_t h = t / rel_hi, j = t - h * rel_hi;
+          if (sorted_has(a.b_idx + s_hbp[h], s_hsz[h], a.W[p0 + j])) adj |= 1ull << j;
+        }
       }
     }
     const int32_t E = s_poff[nnets];
@@ -887,6 +912,127 @@ __global__ void __launch_bounds__(NT) k_gather(GatherArgs a) {
       s_adj = 0ull;
     }
     __syncthreads();
+  }
+}
+
+// Warp-private form of the gather: every warp takes whole pieces on its own,
+// with its own bitmap in shared memory, so no CTA barrier stands between a
+// piece's dependent loads (piece -> vertex -> nets -> net extents) and the
+// other warps' streaming.  Same results as k_gather: the bitmap and mask of
+// a piece are ORed into the vertex's slot the same way.
+template <int NT>
+__global__ void __launch_bounds__(NT) k_gather_w(GatherArgs a) {
+  constexpr int NW = NT / 32;
+  extern __shared__ __align__(16) uint32_t s_all[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t *s_bm = s_all + (size_t)warp * a.words;
+  uint4 *s_bm4 = reinterpret_cast<uint4 *>(s_bm);
+  const int32_t lim = a.words * 32, W4 = a.words >> 2;
+  for (int32_t x = lane; x < a.words; x += 32) s_bm[x] = 0u;
+  __syncwarp();
+  const int32_t sbeg = a.segoff[a.slot_lo], send = a.segoff[a.slot_hi];
+  const uint4 *nb4 = reinterpret_cast<const uint4 *>(a.nbm);
+  const int64_t nwarps = (int64_t)gridDim.x * NW;
+  for (int64_t sg = sbeg + (int64_t)blockIdx.x * NW + warp; sg < send; sg += nwarps) {
+    // ---- the piece: its vertex, its chunk and its nets (one net per lane)
+    const int2 sm = a.segmap[sg];
+    const int32_t u = sm.x, piece = sm.y;
+    const int32_t p0 = a.wlist[u / a.C] * a.C;
+    const int32_t rel_hi = u % a.C;  // the vertex's index in its chunk
+    const int32_t w = a.W[p0 + rel_hi];
+    const int32_t ibeg = a.a_ptr[w] + piece * kPiece;
+    const int32_t nnets = min(a.a_ptr[w + 1] - ibeg, kPiece);
+    const bool whole = (a.segoff[u + 1] - a.segoff[u]) == 1;
+    int32_t sz = 0, bp = 0, hub = -1;
+    if (lane < nnets) {
+      const int32_t v = a.a_idx[ibeg + lane];
+      bp = a.b_ptr[v];
+      sz = a.b_ptr[v + 1] - bp;
+      hub = a.hub_id ? a.hub_id[v] : -1;
+    }
+    const unsigned hubs = __ballot_sync(kFull, hub >= 0);
+    unsigned long long adj = 0ull;
+    if (hubs) {
+      const int32_t hv = __reduce_add_sync(kFull, hub >= 0 ? sz - 1 : 0);
+      if (lane == 0) {
+        atomicAdd(&a.dev->trav_hub, (unsigned long long)hv);
+        atomicAdd(&a.dev->hub_pairs, (unsigned long long)__popc(hubs));
+      }
+      int32_t id_lo = 0, id_hi = 0;
+      if (a.id_order && rel_hi > 0) {
+        id_lo = a.W[p0];
+        id_hi = a.W[p0 + rel_hi - 1];
+      }
+      for (unsigned hm = hubs; hm; hm &= hm - 1u) {
+        const int t = __ffs(hm) - 1;
+        const int32_t slot = __shfl_sync(kFull, hub, t);
+        const int32_t hbp = __shfl_sync(kFull, bp, t), hsz = __shfl_sync(kFull, sz, t);
+        // the hub's colors: each lane ORs its own 16-byte words
+        for (int32_t x = lane; x < W4; x += 32) {
+          const uint4 q = __ldg(nb4 + (int64_t)slot * W4 + x);
+          if (q.x | q.y | q.z | q.w) {
+            uint4 c = s_bm4[x];
+            c.x |= q.x;
+            c.y |= q.y;
+            c.z |= q.z;
+            c.w |= q.w;
+            s_bm4[x] = c;
+          }
+        }
+        // its earlier chunk-mates
+        if (rel_hi > 0) {
+          const int32_t *l = a.b_idx + hbp;
+          if (a.id_order) {
+            int32_t b = 0;
+            if (lane < 2) b = lower_bound(l, hsz, lane == 0 ? id_lo : id_hi + 1);
+            const int32_t lb = __shfl_sync(kFull, b, 0), ub = __shfl_sync(kFull, b, 1);
+            for (int32_t f = lb + lane; f < ub; f += 32) {
+              const int32_t x = a.nc[hbp + f];
+              const int32_t rel = (-2 - x) - p0;
+              if (x < 0 && rel >= 0 && rel < rel_hi) adj |= 1ull << rel;
+            }
+          } else {
+            for (int32_t jj = lane; jj < rel_hi; jj += 32)
+              if (sorted_has(l, hsz, a.W[p0 + jj])) adj |= 1ull << jj;
+          }
+        }
+      }
+      __syncwarp();
+    }
+    // ---- the other nets: stream their mirror words
+    for (int t = 0; t < nnets; t++) {
+      const int32_t n = __shfl_sync(kFull, hub >= 0 ? 0 : sz, t);
+      const int32_t b = __shfl_sync(kFull, bp, t);
+      if (n > 0) warp_stream(a.nc + b, n, s_bm, lim, p0, rel_hi, adj);
+    }
+    const unsigned lo32 = __reduce_or_sync(kFull, (unsigned)(adj & 0xffffffffull));
+    const unsigned hi32 = __reduce_or_sync(kFull, (unsigned)(adj >> 32));
+    __syncwarp();
+    // ---- merge into the vertex's slot, leaving the bitmap zero
+    const int64_t slot = (int64_t)(u - a.slot_lo);
+    uint4 *g4 = reinterpret_cast<uint4 *>(a.gbm + slot * a.words);
+    for (int32_t x = lane; x < W4; x += 32) {
+      const uint4 b = s_bm4[x];
+      if (b.x | b.y | b.z | b.w) {
+        if (whole) {
+          g4[x] = b;
+        } else {
+          uint32_t *g = a.gbm + slot * a.words + 4 * x;
+          if (b.x) atomicOr(g + 0, b.x);
+          if (b.y) atomicOr(g + 1, b.y);
+          if (b.z) atomicOr(g + 2, b.z);
+          if (b.w) atomicOr(g + 3, b.w);
+        }
+        s_bm4[x] = make_uint4(0u, 0u, 0u, 0u);
+      }
+    }
+    if (lane == 0) {
+      const unsigned long long m = ((unsigned long long)hi32 << 32) | lo32;
+      if (m) {
+        if (whole) a.gadj[slot] = m; else atomicOr(&a.gadj[slot], m);
+      }
+    }
+    __syncwarp();
   }
 }
 
@@ -1074,6 +1220,24 @@ cudaError_t launch_color_wave(int policy, const WaveArgs &a, int sms, cudaStream
 
 cudaError_t launch_gather(const GatherArgs &a, int sms, cudaStream_t s) {
   if (a.slot_hi <= a.slot_lo) return cudaSuccess;
+  {  // warp-private pieces when eight bitmaps fit beside each other
+    auto kw = k_gather_w<kGatherNT>;
+    const size_t smem_w = (size_t)(kGatherNT / 32) * a.words * 4;
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (smem_w + 1024 <= (size_t)optin / 2) {  // at least two CTAs per SM
+      cudaError_t e = allow_dynamic_smem(kw);
+      if (e != cudaSuccess) return e;
+      int per_sm = 0;
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kw, kGatherNT, smem_w);
+      if (e != cudaSuccess) return e;
+      if (per_sm >= 1) {
+        kw<<<per_sm * sms, kGatherNT, smem_w, s>>>(a);
+        return cudaGetLastError();
+      }
+    }
+  }
   auto kern = k_gather<kGatherNT>;
   const size_t smem = (size_t)a.words * 4;
   cudaError_t e = allow_dynamic_smem(kern);

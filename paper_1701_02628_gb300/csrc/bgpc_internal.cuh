@@ -189,6 +189,7 @@ struct GatherArgs {
   const int32_t *hub_id;       // net -> hub slot or -1
   const uint32_t *nbm;         // hub color bitmaps [nhub][words] (the wave snapshot)
   DevScalars *dev;             // hub counters
+  int32_t id_order;            // W is in vertex-id order (no rank): a chunk's ids increase
 };
 // Largest bitmap (in words) the wave kernels can hold in shared memory.
 int32_t wave_max_words(int smem_optin);
