@@ -967,16 +967,24 @@ __global__ void __launch_bounds__(NT) k_gather_w(GatherArgs a) {
         const int t = __ffs(hm) - 1;
         const int32_t slot = __shfl_sync(kFull, hub, t);
         const int32_t hbp = __shfl_sync(kFull, bp, t), hsz = __shfl_sync(kFull, sz, t);
-        // the hub's colors: each lane ORs its own 16-byte words
-        for (int32_t x = lane; x < W4; x += 32) {
-          const uint4 q = __ldg(nb4 + (int64_t)slot * W4 + x);
-          if (q.x | q.y | q.z | q.w) {
-            uint4 c = s_bm4[x];
-            c.x |= q.x;
-            c.y |= q.y;
-            c.z |= q.z;
-            c.w |= q.w;
-            s_bm4[x] = c;
+        // the hub's colors: each lane ORs its own 16-byte words, four
+        // loads in flight
+        const uint4 *src = nb4 + (int64_t)slot * W4;
+        for (int32_t x0 = lane; x0 < W4; x0 += 128) {
+          uint4 q[4];
+#pragma unroll
+          for (int k = 0; k < 4; k++)
+            q[k] = (x0 + 32 * k < W4) ? __ldg(src + x0 + 32 * k) : make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+          for (int k = 0; k < 4; k++) {
+            if (q[k].x | q[k].y | q[k].z | q[k].w) {
+              uint4 c = s_bm4[x0 + 32 * k];
+              c.x |= q[k].x;
+              c.y |= q[k].y;
+              c.z |= q[k].z;
+              c.w |= q[k].w;
+              s_bm4[x0 + 32 * k] = c;
+            }
           }
         }
         // its earlier chunk-mates
