@@ -247,12 +247,22 @@ int color_impl(bgpc_ctx_t *ctx, const bgpc_graph_t &g, const bgpc_opts_t &o, int
       maxwave = woff[q + 1] - woff[q] > maxwave ? woff[q + 1] - woff[q] : maxwave;
     {
       const size_t gw = (size_t)maxwave * C * (size_t)words;
-      if (gw > ctx->gbm.cap || gw > ctx->gbm_zeroed || (size_t)maxwave * C > ctx->gadj.cap) {
+      const size_t slots = (size_t)maxwave * C;
+      if (gw > ctx->gbm.cap || gw > ctx->gbm_zeroed || slots > ctx->gadj.cap ||
+          slots > ctx->gcnt.cap) {
         CU(grow(ctx->gbm, gw));
-        CU(grow(ctx->gadj, (size_t)maxwave * C));
+        CU(grow(ctx->gadj, slots));
+        CU(grow(ctx->gcnt, slots));
         CU(cudaMemsetAsync(ctx->gbm.p, 0, ctx->gbm.cap * sizeof(uint32_t), s));
         CU(cudaMemsetAsync(ctx->gadj.p, 0, ctx->gadj.cap * sizeof(unsigned long long), s));
+        CU(cudaMemsetAsync(ctx->gcnt.p, 0, ctx->gcnt.cap * sizeof(int32_t), s));
         ctx->gbm_zeroed = ctx->gbm.cap;
+      }
+      // first fit: the gather's per-slot summaries and the bitmaps kept for
+      // the reverse first fit (both written before they are read)
+      if (o.policy == BGPC_FF) {
+        CU(grow(ctx->gsum, slots * kSumInts));
+        CU(grow(ctx->lbm, gw));
       }
     }
     // the colors published so far, per hub net, at this round's bitmap width
@@ -299,6 +309,13 @@ int color_impl(bgpc_ctx_t *ctx, const bgpc_graph_t &g, const bgpc_opts_t &o, int
         ga.nbm = ctx->nbm.p;
         ga.dev = ctx->dev;
         ga.id_order = o.rank ? 0 : 1;
+        ga.summ = o.policy == BGPC_FF;
+        ga.T = o.big_net;
+        ga.s_own = ctx->s_own.p;
+        ga.kofs = ctx->kofs.p;
+        ga.gcnt = ctx->gcnt.p;
+        ga.gsum = ctx->gsum.p;
+        ga.lbm = ctx->lbm.p;
         ev = tm.begin();
         CU(launch_gather(ga, sms, s));
         tm.end(ev, PH_GATHER);
@@ -325,6 +342,8 @@ int color_impl(bgpc_ctx_t *ctx, const bgpc_graph_t &g, const bgpc_opts_t &o, int
         a.small_ok = small_ok;
         a.gbm = ctx->gbm.p;
         a.gadj = ctx->gadj.p;
+        a.gsum = ctx->gsum.p;
+        a.lbm = ctx->lbm.p;
         ev = tm.begin();
         CU(launch_color_wave(o.policy, a, sms, s));
         tm.end(ev, PH_COLOR);
@@ -469,6 +488,7 @@ int bgpc_ctx_destroy(bgpc_ctx_t *ctx) {
   release(ctx->hub_id); release(ctx->hub_net); release(ctx->nbm);
   release(ctx->cptr); release(ctx->cidx); release(ctx->dtab); release(ctx->vtab);
   release(ctx->wlist); release(ctx->segoff); release(ctx->segmap); release(ctx->gbm);
+  release(ctx->gcnt); release(ctx->gsum); release(ctx->lbm);
   release(ctx->gadj);
   if (ctx->h_wlist) cudaFreeHost(ctx->h_wlist);
   for (bgpc_ctx_t *sub : ctx->subs) bgpc_ctx_destroy(sub);

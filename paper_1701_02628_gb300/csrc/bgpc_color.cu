@@ -246,27 +246,30 @@ __device__ __forceinline__ int32_t win_kth_free_down(uint32_t word, int32_t top,
   return __shfl_sync(kFull, res, __ffs(b) - 1);
 }
 
-// ------------------------------------- candidate summaries (warp, global)
+// ------------------------------------------- candidate summaries (warp)
 // A large vertex's forbidden set F_S (colors of its two-hop neighbours in the
-// wave snapshot) sits in a global bitmap g of `words` words; colors beyond
-// 32 * words are free.  Its chunk adds at most 63 more colors (the overlay
-// O), so first fit needs only the kCand smallest free colors of F_S, and the
-// reverse first fit needs the free colors of F_S from the k-th below the top
-// on (plus, for overlay colors above that window, one bit of g each).
+// wave snapshot) is a bitmap g of `words` words; colors beyond 32 * words are
+// free.  Its chunk adds at most 63 more colors (the overlay O), so first fit
+// needs only the kSumCand smallest free colors of F_S, and the reverse first
+// fit needs the free colors of F_S from the k-th below the top on (plus, for
+// overlay colors above that window, one bit of g each).  The gather computes
+// these summaries from the bitmap in shared memory; the resolve keeps the
+// first kCand entries of each list in shared memory and reads the rest from
+// the summary only when its chunk-mates take all kCand.
 constexpr int kCand = 32;
 
-// The kCand smallest colors not in g, ascending, into out[].
-__device__ __forceinline__ void warp_first_free(const uint32_t *__restrict__ g, int32_t words,
-                                                int32_t *out) {
+// The N smallest colors not in g, ascending, into out[].
+template <int N>
+__device__ __forceinline__ void warp_first_free(const uint32_t *g, int32_t words, int32_t *out) {
   const int lane = threadIdx.x & 31;
   int32_t got = 0;
-  for (int32_t w0 = 0; got < kCand; w0 += 32) {
+  for (int32_t w0 = 0; got < N; w0 += 32) {
     const int32_t wi = w0 + lane;
     uint32_t fr = (wi < words) ? ~g[wi] : 0xffffffffu;
     const int32_t cnt = __popc(fr);
     const int32_t inc = warp_incl_scan(cnt);
     int32_t r = got + inc - cnt;
-    while (fr && r < kCand) {
+    while (fr && r < N) {
       out[r++] = wi * 32 + __ffs(fr) - 1;
       fr &= fr - 1u;
     }
@@ -275,16 +278,16 @@ __device__ __forceinline__ void warp_first_free(const uint32_t *__restrict__ g, 
   __syncwarp();
 }
 
-// Colors not in g counted down from top: the k-th .. (k+kCand-1)-th (0-based)
+// Colors not in g counted down from top: the k-th .. (k+N-1)-th (0-based)
 // into out[], descending.  Returns how many of them exist (0 if fewer than
 // k + 1 free colors lie in [0, top]).
-__device__ __forceinline__ int32_t warp_kth_free_down(const uint32_t *__restrict__ g,
-                                                      int32_t words, int32_t top, int32_t k,
-                                                      int32_t *out) {
+template <int N>
+__device__ __forceinline__ int32_t warp_kth_free_down(const uint32_t *g, int32_t words,
+                                                      int32_t top, int32_t k, int32_t *out) {
   const int lane = threadIdx.x & 31;
   int32_t seen = 0;
   const int32_t wtop = top >> 5;
-  for (int32_t w0 = wtop; w0 >= 0 && seen < k + kCand; w0 -= 32) {
+  for (int32_t w0 = wtop; w0 >= 0 && seen < k + N; w0 -= 32) {
     const int32_t wi = w0 - lane;  // lane 0 holds the highest word
     uint32_t fr = 0u;
     if (wi >= 0) {
@@ -294,8 +297,8 @@ __device__ __forceinline__ int32_t warp_kth_free_down(const uint32_t *__restrict
     const int32_t cnt = __popc(fr);
     const int32_t inc = warp_incl_scan(cnt);
     int32_t r = seen + inc - cnt;  // rank of this lane's highest free color
-    if (r + cnt > k && r < k + kCand) {
-      while (fr && r < k + kCand) {
+    if (r + cnt > k && r < k + N) {
+      while (fr && r < k + N) {
         const int32_t b = 31 - __clz(fr);
         if (r >= k) out[r - k] = wi * 32 + b;
         r++;
@@ -306,7 +309,31 @@ __device__ __forceinline__ int32_t warp_kth_free_down(const uint32_t *__restrict
   }
   __syncwarp();
   const int32_t have = seen - k;
-  return have <= 0 ? 0 : (have < kCand ? have : kCand);
+  return have <= 0 ? 0 : (have < N ? have : N);
+}
+
+// One warp: the first-fit summary of a large vertex from its forbidden
+// bitmap bm (`words` words, read only) into rec[kSumInts]; the owner of a net
+// larger than T (so > T) with a k-th free color also leaves the bitmap words
+// up to color so - 1 in lb, for the resolve's tests of overlay colors.
+__device__ __forceinline__ void warp_summarize(const uint32_t *bm, int32_t words, int32_t so,
+                                               int32_t T, int32_t k, unsigned long long adj,
+                                               int32_t *rec, uint32_t *lb) {
+  const int lane = threadIdx.x & 31;
+  warp_first_free<kSumCand>(bm, words, rec);
+  int32_t rc = 0;
+  if (so > T) rc = warp_kth_free_down<kSumCand>(bm, words, so - 1, k, rec + kSumCand);
+  if (lane == 0) {
+    rec[2 * kSumCand] = rc;
+    *reinterpret_cast<unsigned long long *>(rec + 2 * kSumCand + 2) = adj;
+  }
+  if (rc > 0) {
+    const int32_t n4 = min(words >> 2, ((so - 1) >> 7) + 1);
+    const uint4 *b4 = reinterpret_cast<const uint4 *>(bm);
+    uint4 *l4 = reinterpret_cast<uint4 *>(lb);
+    for (int32_t x = lane; x < n4; x += 32) l4[x] = b4[x];
+  }
+  __syncwarp();
 }
 
 // Index of the candidate equal to c in a sorted list (ascending if asc),
@@ -321,6 +348,30 @@ __device__ __forceinline__ int32_t cand_index(const int32_t *list, int32_t cnt, 
   }
   return (cnt > 0 && list[lo] == c) ? lo : -1;
 }
+
+__device__ __forceinline__ unsigned long long low_mask64(int32_t n) {
+  return n >= 64 ? ~0ull : ((1ull << n) - 1ull);
+}
+
+// The entries of list[0, cnt) (sorted, ascending if asc) equal to one of the
+// warp's overlay colors oc[] that are not above hi, as a mask (the same in
+// every lane).
+__device__ __forceinline__ unsigned long long overlay_marks(const int32_t *list, int32_t cnt,
+                                                            const int32_t (&oc)[2], int32_t hi,
+                                                            bool asc) {
+  unsigned long long m = 0ull;
+#pragma unroll
+  for (int h = 0; h < 2; h++) {
+    const int32_t c = oc[h];
+    if (c < 0 || c > hi) continue;
+    const int32_t idx = cand_index(list, cnt, c, asc);
+    if (idx >= 0) m |= 1ull << idx;
+  }
+  const unsigned lo = __reduce_or_sync(kFull, (unsigned)(m & 0xffffffffull));
+  const unsigned hi32 = __reduce_or_sync(kFull, (unsigned)(m >> 32));
+  return ((unsigned long long)hi32 << 32) | lo;
+}
+
 
 // --------------------------------------------------------- resolve kernel
 
@@ -348,6 +399,7 @@ __global__ void __launch_bounds__(NT) k_color_wave(WaveArgs a) {
   __shared__ int32_t s_cand[KC][kCand];   // first-fit candidates of large vertices
   __shared__ int32_t s_rcand[KC][kCand];  // reverse first-fit candidates (descending)
   __shared__ int32_t s_rcnt[KC];
+  __shared__ int32_t s_cx[(POLICY == BGPC_FF) ? kSumCand : 1];  // a whole summary list
   __shared__ unsigned long long s_large;
   extern __shared__ __align__(16) uint32_t s_big[];  // a.words: one large vertex's F
 
@@ -485,21 +537,17 @@ __global__ void __launch_bounds__(NT) k_color_wave(WaveArgs a) {
     }
     __syncthreads();
 
-    // ---- step S (first fit): condense every large vertex's forbidden set
+    // ---- step S (first fit): the large vertices' summaries from the gather
     const unsigned long long large = s_large;
     if constexpr (POLICY == BGPC_FF) {
       for (int32_t iv = warp; iv < n; iv += NW) {
         if (!((large >> iv) & 1ull)) continue;
-        const int64_t slot = slot0 + iv;
-        const uint32_t *g = a.gbm + slot * a.words;
-        warp_first_free(g, a.words, s_cand[iv]);
-        int32_t rc = 0;
-        if (s_sown[iv] > a.T)
-          rc = warp_kth_free_down(g, a.words, s_sown[iv] - 1, s_k[iv], s_rcand[iv]);
+        const int32_t *rec = a.gsum + (slot0 + iv) * kSumInts;
+        s_cand[iv][lane] = rec[lane];
+        s_rcand[iv][lane] = rec[kSumCand + lane];
         if (lane == 0) {
-          s_rcnt[iv] = rc;
-          s_adj[iv] = a.gadj[slot];
-          a.gadj[slot] = 0ull;
+          s_rcnt[iv] = rec[2 * kSumCand];
+          s_adj[iv] = *reinterpret_cast<const unsigned long long *>(rec + 2 * kSumCand + 2);
         }
       }
       __syncthreads();
@@ -559,31 +607,22 @@ __global__ void __launch_bounds__(NT) k_color_wave(WaveArgs a) {
               const int32_t jj = lane + 32 * h;
               oc[h] = (jj < ii && ((am >> jj) & 1ull)) ? s_col[jj] : -1;
             }
-            bool fallback = false;
+            const int32_t *rec = a.gsum + (slot0 + ii) * kSumInts;
             const int32_t so = s_sown[ii];
             const int32_t rcnt = (so > a.T) ? s_rcnt[ii] : 0;
             if (rcnt > 0) {
               // k-th free color of F_S u O counted down from so - 1: skip the
               // overlay colors that are free in F_S above the window, and the
               // window entries that the overlay takes
-              const int32_t *rcd = s_rcand[ii];
-              const int32_t ak = rcd[0];
-              const uint32_t *g = a.gbm + (slot0 + ii) * a.words;
+              const int32_t ak = s_rcand[ii][0];
+              const uint32_t *g = a.lbm + (slot0 + ii) * a.words;
               // e = distinct overlay colors in (ak, so - 1] that are free in
               // F_S (two chunk-mates may share a color: F is a set)
               bool up[2];
-              uint32_t mark = 0u;
 #pragma unroll
               for (int h = 0; h < 2; h++) {
                 const int32_t c = oc[h];
-                up[h] = false;
-                if (c < 0 || c > so - 1) continue;
-                if (c > ak) {
-                  up[h] = !((g[c >> 5] >> (c & 31)) & 1u);
-                } else {
-                  const int32_t idx = cand_index(rcd, rcnt, c, false);
-                  if (idx >= 0) mark |= 1u << idx;
-                }
+                up[h] = c > ak && c <= so - 1 && !((g[c >> 5] >> (c & 31)) & 1u);
               }
               const unsigned m0 = __match_any_sync(kFull, up[0] ? oc[0] : -1 - lane);
               const unsigned m1 = __match_any_sync(kFull, up[1] ? oc[1] : -1 - lane);
@@ -597,28 +636,46 @@ __global__ void __launch_bounds__(NT) k_color_wave(WaveArgs a) {
               }
               const int32_t e = __popc(__ballot_sync(kFull, first0)) +
                                 __popc(__ballot_sync(kFull, first1));
-              mark = __reduce_or_sync(kFull, mark);
-              const uint32_t avail = ~mark & (rcnt == 32 ? 0xffffffffu : ((1u << rcnt) - 1u));
-              if (__popc(avail) > e) {
-                uint32_t av = avail;
-                for (int32_t t = 0; t < e; t++) av &= av - 1u;  // drop the e lowest
-                x = rcd[__ffs(av) - 1];
+              // the (e+1)-th window entry that no overlay color takes: first
+              // among the kCand entries kept here, else among all of them
+              const int32_t n1 = min(rcnt, kCand);
+              const int32_t *lst = s_rcand[ii];
+              unsigned long long av = ~overlay_marks(lst, n1, oc, ak, false) & low_mask64(n1);
+              if (__popcll(av) <= e && rcnt > kCand) {
+                s_cx[lane] = rec[kSumCand + lane];
+                s_cx[lane + 32] = rec[kSumCand + 32 + lane];
+                __syncwarp();
+                lst = s_cx;
+                av = ~overlay_marks(lst, rcnt, oc, ak, false) & low_mask64(rcnt);
               }
-              else if (rcnt == kCand) fallback = true;
-            }
-            if (x < 0 && !fallback) {
-              uint32_t mark = 0u;
-#pragma unroll
-              for (int h = 0; h < 2; h++) {
-                if (oc[h] < 0) continue;
-                const int32_t idx = cand_index(s_cand[ii], kCand, oc[h], true);
-                if (idx >= 0) mark |= 1u << idx;
+              if (__popcll(av) > e) {
+                for (int32_t t = 0; t < e; t++) av &= av - 1ull;  // drop the e lowest
+                x = lst[__ffsll((long long)av) - 1];
+              } else if (rcnt == kSumCand) {
+                // e + (taken entries) <= |O| <= 63 < 64 entries
+                if (lane == 0) atomicOr(a.err, ERR_INTERNAL);
+                x = 0;
               }
-              mark = __reduce_or_sync(kFull, mark);
-              if (mark == 0xffffffffu) fallback = true;
-              else x = s_cand[ii][__ffs(~mark) - 1];
             }
-            if (fallback) break;
+            if (x < 0) {
+              unsigned long long fr = ~overlay_marks(s_cand[ii], kCand, oc, INT32_MAX, true) &
+                                      low_mask64(kCand);
+              if (fr) {
+                x = s_cand[ii][__ffsll((long long)fr) - 1];
+              } else {
+                s_cx[lane] = rec[lane];
+                s_cx[lane + 32] = rec[32 + lane];
+                __syncwarp();
+                fr = ~overlay_marks(s_cx, kSumCand, oc, INT32_MAX, true);
+                if (fr) {
+                  x = s_cx[__ffsll((long long)fr) - 1];
+                } else {  // at most 63 overlay colors take at most 63 entries
+                  if (lane == 0) atomicOr(a.err, ERR_INTERNAL);
+                  x = 0;
+                }
+              }
+            }
+            __syncwarp();
           }
           col_max = max(col_max, x);
           if (POLICY == BGPC_B2) col_next = min(x + 1, col_max / 3 + 1);
@@ -684,14 +741,6 @@ __global__ void __launch_bounds__(NT) k_color_wave(WaveArgs a) {
         __syncthreads();
       }
       i = L + 1;
-    }
-    if constexpr (POLICY == BGPC_FF) {
-      // leave the slots of this chunk's large vertices zero for the next wave
-      for (unsigned long long mk = large; mk; mk &= mk - 1ull) {
-        const int32_t iv = __ffsll((long long)mk) - 1;
-        uint4 *g = reinterpret_cast<uint4 *>(a.gbm + (slot0 + iv) * a.words);
-        for (int32_t x = tid; x < (a.words >> 2); x += NT) g[x] = make_uint4(0u, 0u, 0u, 0u);
-      }
     }
     if (tid < n) a.stage[p0 + tid] = s_col[tid];
     __syncthreads();
@@ -781,7 +830,7 @@ __global__ void __launch_bounds__(NT) k_gather(GatherArgs a) {
   __shared__ int32_t s_pstart[kPiece];
   __shared__ int32_t s_poff[kPiece + 1];
   __shared__ int32_t s_hslot[kPiece], s_hbp[kPiece], s_hsz[kPiece];  // hub nets of the piece
-  __shared__ int32_t s_info[5];  // p0, rel_hi, whole, nnets, hubs
+  __shared__ int32_t s_info[7];  // p0, rel_hi, whole, nnets, hubs, vertex, pieces
   __shared__ int64_t s_slot;
   __shared__ unsigned long long s_adj;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -834,6 +883,8 @@ __global__ void __launch_bounds__(NT) k_gather(GatherArgs a) {
         s_info[2] = (a.segoff[u + 1] - a.segoff[u]) == 1;
         s_info[3] = nnets;
         s_info[4] = __popc(hubs);
+        s_info[5] = w;
+        s_info[6] = a.segoff[u + 1] - a.segoff[u];
         s_slot = (int64_t)(u - a.slot_lo);
       }
     }
@@ -893,26 +944,82 @@ __global__ void __launch_bounds__(NT) k_gather(GatherArgs a) {
     const unsigned hi32 = __reduce_or_sync(kFull, (unsigned)(adj >> 32));
     if (lane == 0 && (lo32 | hi32)) atomicOr(&s_adj, ((unsigned long long)hi32 << 32) | lo32);
     __syncthreads();
-    // ---- merge into the vertex's slot, leaving the shared bitmap zero
     const int64_t slot = s_slot;
     uint32_t *g = a.gbm + slot * a.words;
     const bool whole = s_info[2] != 0;
-    for (int32_t x = tid; x < a.words; x += NT) {
-      const uint32_t b = s_bm[x];
-      if (b) {
-        if (whole) g[x] = b; else atomicOr(&g[x], b);
-        s_bm[x] = 0u;
+    bool take = false;  // first fit: this CTA writes the vertex's summary
+    if (a.summ && !whole) {
+      // ---- several pieces: merge into the slot; the last piece to merge
+      // takes the slot back (leaving it zero)
+      for (int32_t x = tid; x < a.words; x += NT) {
+        const uint32_t b = s_bm[x];
+        if (b) {
+          atomicOr(&g[x], b);
+          s_bm[x] = 0u;
+        }
       }
+      if (tid == 0 && s_adj) atomicOr(&a.gadj[slot], s_adj);
+      __threadfence();
+      __syncthreads();
+      if (tid == 0) s_info[2] = atomicAdd(a.gcnt + slot, 1) == s_info[6] - 1;
+      __syncthreads();
+      take = s_info[2] != 0;
+      if (take) {
+        __threadfence();
+        for (int32_t x = tid; x < a.words; x += NT) {
+          const uint32_t b = __ldcg(g + x);
+          if (b) {
+            s_bm[x] = b;
+            g[x] = 0u;
+          }
+        }
+        if (tid == 0) {
+          s_adj = __ldcg(a.gadj + slot);
+          a.gadj[slot] = 0ull;
+          a.gcnt[slot] = 0;
+        }
+        __syncthreads();
+      }
+    } else if (a.summ) {
+      take = true;  // one piece: the bitmap is complete
     }
-    if (tid == 0) {
-      const unsigned long long m = s_adj;
-      if (m) {
-        if (whole) a.gadj[slot] = m; else atomicOr(&a.gadj[slot], m);
+    if (take) {
+      if (warp == 0) {
+        const int32_t so = a.s_own[s_info[5]];
+        warp_summarize(s_bm, a.words, so, a.T, (so > a.T) ? a.kofs[p0 + rel_hi] : 0, s_adj,
+                       a.gsum + slot * kSumInts, a.lbm + slot * a.words);
       }
-      s_adj = 0ull;
+      __syncthreads();
+      for (int32_t x = tid; x < a.words; x += NT) s_bm[x] = 0u;
+    } else if (!a.summ) {
+      // ---- merge into the vertex's slot, leaving the shared bitmap zero
+      for (int32_t x = tid; x < a.words; x += NT) {
+        const uint32_t b = s_bm[x];
+        if (b) {
+          if (whole) g[x] = b; else atomicOr(&g[x], b);
+          s_bm[x] = 0u;
+        }
+      }
+      if (tid == 0) {
+        const unsigned long long m = s_adj;
+        if (m) {
+          if (whole) a.gadj[slot] = m; else atomicOr(&a.gadj[slot], m);
+        }
+      }
     }
     __syncthreads();
+    if (tid == 0) s_adj = 0ull;
+    __syncthreads();
   }
+}
+
+// Zero the non-zero 16-byte words of a warp's shared bitmap.
+__device__ __forceinline__ void warp_clear(uint4 *bm4, int32_t n4) {
+  for (int32_t x = (int32_t)(threadIdx.x & 31); x < n4; x += 32) {
+    const uint4 b = bm4[x];
+    if (b.x | b.y | b.z | b.w) bm4[x] = make_uint4(0u, 0u, 0u, 0u);
+  }
+  __syncwarp();
 }
 
 // Warp-private form of the gather: every warp takes whole pieces on its own,
@@ -1015,14 +1122,23 @@ __global__ void __launch_bounds__(NT) k_gather_w(GatherArgs a) {
     }
     const unsigned lo32 = __reduce_or_sync(kFull, (unsigned)(adj & 0xffffffffull));
     const unsigned hi32 = __reduce_or_sync(kFull, (unsigned)(adj >> 32));
+    const unsigned long long adjm = ((unsigned long long)hi32 << 32) | lo32;
     __syncwarp();
-    // ---- merge into the vertex's slot, leaving the bitmap zero
     const int64_t slot = (int64_t)(u - a.slot_lo);
+    if (a.summ && whole) {
+      // first fit, one piece: the summary straight from the bitmap
+      const int32_t so = a.s_own[w];
+      warp_summarize(s_bm, a.words, so, a.T, (so > a.T) ? a.kofs[p0 + rel_hi] : 0, adjm,
+                     a.gsum + slot * kSumInts, a.lbm + slot * a.words);
+      warp_clear(s_bm4, W4);
+      continue;
+    }
+    // ---- merge into the vertex's slot, leaving the bitmap zero
     uint4 *g4 = reinterpret_cast<uint4 *>(a.gbm + slot * a.words);
     for (int32_t x = lane; x < W4; x += 32) {
       const uint4 b = s_bm4[x];
       if (b.x | b.y | b.z | b.w) {
-        if (whole) {
+        if (whole && !a.summ) {
           g4[x] = b;
         } else {
           uint32_t *g = a.gbm + slot * a.words + 4 * x;
@@ -1034,10 +1150,38 @@ __global__ void __launch_bounds__(NT) k_gather_w(GatherArgs a) {
         s_bm4[x] = make_uint4(0u, 0u, 0u, 0u);
       }
     }
-    if (lane == 0) {
-      const unsigned long long m = ((unsigned long long)hi32 << 32) | lo32;
-      if (m) {
-        if (whole) a.gadj[slot] = m; else atomicOr(&a.gadj[slot], m);
+    if (lane == 0 && adjm) {
+      if (whole && !a.summ) a.gadj[slot] = adjm; else atomicOr(&a.gadj[slot], adjm);
+    }
+    if (a.summ) {
+      // first fit, several pieces: the last piece to merge takes the slot
+      // back (leaving it zero) and writes the summary
+      __threadfence();
+      __syncwarp();
+      int32_t last = 0;
+      if (lane == 0) last = atomicAdd(a.gcnt + slot, 1) == a.segoff[u + 1] - a.segoff[u] - 1;
+      last = __shfl_sync(kFull, last, 0);
+      if (last) {
+        __threadfence();
+        unsigned long long m = 0ull;
+        if (lane == 0) {
+          m = __ldcg(a.gadj + slot);
+          a.gadj[slot] = 0ull;
+          a.gcnt[slot] = 0;
+        }
+        m = __shfl_sync(kFull, m, 0);
+        for (int32_t x = lane; x < W4; x += 32) {
+          const uint4 q = __ldcg(g4 + x);
+          if (q.x | q.y | q.z | q.w) {
+            s_bm4[x] = q;
+            g4[x] = make_uint4(0u, 0u, 0u, 0u);
+          }
+        }
+        __syncwarp();
+        const int32_t so = a.s_own[w];
+        warp_summarize(s_bm, a.words, so, a.T, (so > a.T) ? a.kofs[p0 + rel_hi] : 0, m,
+                       a.gsum + slot * kSumInts, a.lbm + slot * a.words);
+        warp_clear(s_bm4, W4);
       }
     }
     __syncwarp();

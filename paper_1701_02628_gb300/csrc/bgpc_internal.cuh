@@ -40,6 +40,13 @@ constexpr int kSmallMaxDeg = 16;    // small path: at most this many nets
 constexpr int kPairCap = kMaxChunk * kSmallMaxDeg;  // (vertex, net) pairs per chunk
 constexpr int kPiece = 16;          // gather work item: up to this many nets of one vertex
 constexpr int kDetectWarpMax = 32;  // nets up to this size use the warp tier
+// First-fit summary of a large vertex's forbidden set F_S (written by the
+// gather, read by the resolve): the kSumCand smallest free colors, the free
+// colors from the k-th below the owner-net top on (reverse first fit), their
+// count, and the 64-bit chunk-mate mask.  A chunk adds at most C - 1 <= 63
+// colors to F_S, so 64 candidates always leave one free.
+constexpr int kSumCand = 64;
+constexpr int kSumInts = 2 * kSumCand + 4;  // cand | rcand | rcnt, pad | adj (u64)
 
 // Device scalars shared by the kernels of one call.
 struct DevScalars {
@@ -92,7 +99,10 @@ struct bgpc_ctx {
   bgpc::Buf<int32_t> hub_id, hub_net;  // net -> hub slot (-1: not a hub), slot -> net
   bgpc::Buf<uint32_t> nbm;             // hub color bitmaps [nhub][words]
   bgpc::Buf<unsigned long long> gadj;  // per-slot chunk-mate adjacency of large vertices
-  size_t gbm_zeroed = 0;               // words of gbm known to be zero
+  bgpc::Buf<int32_t> gcnt;             // per-slot count of merged pieces (first fit)
+  bgpc::Buf<int32_t> gsum;             // per-slot first-fit summaries [kSumInts]
+  bgpc::Buf<uint32_t> lbm;             // per-slot bitmaps kept for the reverse first fit
+  size_t gbm_zeroed = 0;               // words of gbm (and slots of gadj, gcnt) known zero
   int32_t *h_wlist = nullptr;          // pinned host staging of wlist
   size_t h_wlist_cap = 0;
   bgpc::Buf<int32_t> cptr, cidx;       // D2GC closed neighbourhoods
@@ -172,6 +182,8 @@ struct WaveArgs {
   int32_t small_ok;            // the small path is usable this round
   uint32_t *gbm;               // per-slot bitmaps of large vertices (slot = list index*C + i)
   unsigned long long *gadj;    // per-slot chunk-mate masks of large vertices
+  const int32_t *gsum;         // first fit: per-slot summaries written by the gather
+  const uint32_t *lbm;         // first fit: per-slot bitmaps of reverse first-fit vertices
 };
 struct GatherArgs {
   const int32_t *a_ptr, *a_idx, *b_ptr;
@@ -190,6 +202,15 @@ struct GatherArgs {
   const uint32_t *nbm;         // hub color bitmaps [nhub][words] (the wave snapshot)
   DevScalars *dev;             // hub counters
   int32_t id_order;            // W is in vertex-id order (no rank): a chunk's ids increase
+  // first fit only (summ != 0): the gather ends with each large vertex's
+  // summary (kSumInts per slot) instead of leaving its bitmap for the resolve
+  int32_t summ;
+  int32_t T;                   // reverse first fit for owners of nets larger than T
+  const int32_t *s_own;        // vertex -> size of its owner net
+  const int32_t *kofs;         // queue position -> reverse first-fit offset k
+  int32_t *gcnt;               // per-slot merged-piece counts (zero at rest)
+  int32_t *gsum;               // per-slot summaries
+  uint32_t *lbm;               // per-slot bitmaps for the resolve's overlay tests
 };
 // Largest bitmap (in words) the wave kernels can hold in shared memory.
 int32_t wave_max_words(int smem_optin);
