@@ -102,8 +102,15 @@ typedef struct {
                                 stopped_wave = waves) */
     int32_t batch_streams;   /* bgpc_color_batched only: graphs colored concurrently
                                 (0 = 8); a mapping parameter, results do not change */
-    int32_t reserved[4];
+    int32_t detect;          /* conflict detection of rounds after the first:
+                                BGPC_DETECT_AUTO (0), BGPC_DETECT_NETS (every net
+                                scanned) or BGPC_DETECT_PAIRS (only the (W member,
+                                net) pairs, through a hash table); a mapping
+                                parameter, results do not change */
+    int32_t reserved[3];
 } bgpc_opts_t;
+
+enum { BGPC_DETECT_AUTO = 0, BGPC_DETECT_NETS = 1, BGPC_DETECT_PAIRS = 2 };
 
 /* Statistics of one call (host struct). */
 typedef struct {

@@ -60,6 +60,7 @@ int check_graph_args(const bgpc_graph_t *g) {
 int check_opts(const bgpc_opts_t *o) {
   if (!o) return BGPC_EINVAL;
   if (o->policy < BGPC_FF || o->policy > BGPC_B2X) return BGPC_EINVAL;
+  if (o->detect < BGPC_DETECT_AUTO || o->detect > BGPC_DETECT_PAIRS) return BGPC_EINVAL;
   if (o->chunk < 1 || o->chunk > kMaxChunk) return BGPC_EINVAL;
   if (o->waves < 1 || o->big_net < 0 || o->max_rounds < 1 || o->stop_after_waves < 0)
     return BGPC_EINVAL;
@@ -198,6 +199,7 @@ int color_impl(bgpc_ctx_t *ctx, const bgpc_graph_t &g, const bgpc_opts_t &o, int
 
   int32_t *W = ctx->W0.p, *Wn = ctx->W1.p;
   int32_t m = n_a, gmax = -1, r = 0;
+  int64_t incid_w = -1;  // sum over W of |nets(w)| (known from the second round on)
   int64_t waves_done = 0;
   const int32_t C = o.chunk, Q = o.waves;
   while (m > 0) {
@@ -370,9 +372,24 @@ int color_impl(bgpc_ctx_t *ctx, const bgpc_graph_t &g, const bgpc_opts_t &o, int
     }
     // ---- RemoveConflicts and the next work queue
     ev = tm.begin();
-    nk += launch_detect(g.b_ptr, n_b, ctx->nc.p, ctx->npos.p, ctx->bigd.p, nbig_d, ctx->dtab.p,
-                        cbw, nslots, ctx->lose.p, sms, s);
-    nk += launch_compact(ctx->lose.p, W, m, ctx->newpos.p, Wn, ctx->blocksum.p, ctx->dev, s);
+    // after the first round W is usually a small part of the graph: then
+    // only its (member, net) pairs are examined instead of every net
+    int64_t cap = 1024;  // hash table at load <= 1/2
+    while (incid_w >= 0 && cap < 2 * incid_w) cap <<= 1;
+    const bool pairs = incid_w >= 0 && cap <= ((int64_t)1 << 31) &&
+                       o.detect != BGPC_DETECT_NETS &&
+                       (o.detect == BGPC_DETECT_PAIRS || incid_w * 4 <= (int64_t)nnz);
+    if (pairs) {
+      CU(grow(ctx->pkeys, (size_t)cap));
+      CU(grow(ctx->pvals, (size_t)cap));
+      nk += launch_detect_pairs(g.a_ptr, g.a_idx, W, m, colors, ctx->pkeys.p, ctx->pvals.p,
+                                (uint32_t)(cap - 1), ctx->lose.p, &ctx->dev->err, sms, s);
+    } else {
+      nk += launch_detect(g.b_ptr, n_b, ctx->nc.p, ctx->npos.p, ctx->bigd.p, nbig_d,
+                          ctx->dtab.p, cbw, nslots, ctx->lose.p, sms, s);
+    }
+    nk += launch_compact(ctx->lose.p, W, m, ctx->newpos.p, Wn, ctx->blocksum.p, g.a_ptr,
+                         ctx->dev, s);
     nk += launch_relabel(g.a_ptr, ctx->tpos.p, W, m, ctx->lose.p, ctx->newpos.p, ctx->nc.p,
                          ctx->npos.p, colors, sms, s);
     nk += launch_gmax(colors, n_a, ctx->dev, s);
@@ -400,6 +417,7 @@ int color_impl(bgpc_ctx_t *ctx, const bgpc_graph_t &g, const bgpc_opts_t &o, int
     st.w_total += m;
     r++;
     const int32_t mn = ctx->host->m_next;
+    incid_w = (int64_t)ctx->host->incid_next;
     if (mn < 0 || mn > m) return BGPC_EINTERNAL;
     int32_t *t = W;
     W = Wn;
@@ -488,7 +506,8 @@ int bgpc_ctx_destroy(bgpc_ctx_t *ctx) {
   release(ctx->hub_id); release(ctx->hub_net); release(ctx->nbm);
   release(ctx->cptr); release(ctx->cidx); release(ctx->dtab); release(ctx->vtab);
   release(ctx->wlist); release(ctx->segoff); release(ctx->segmap); release(ctx->gbm);
-  release(ctx->gcnt); release(ctx->gsum); release(ctx->lbm);
+  release(ctx->gcnt); release(ctx->gsum); release(ctx->lbm); release(ctx->pkeys);
+  release(ctx->pvals);
   release(ctx->gadj);
   if (ctx->h_wlist) cudaFreeHost(ctx->h_wlist);
   for (bgpc_ctx_t *sub : ctx->subs) bgpc_ctx_destroy(sub);

@@ -933,7 +933,7 @@ __global__ void __launch_bounds__(NT) k_gather(GatherArgs a) {
     const int32_t lo_e = min(E, warp * per), hi_e = min(E, lo_e + per);
     if (lo_e < hi_e) {
       int32_t t = 0;  // first net of the slice: largest t with s_poff[t] <= lo_e
-      for (int32_t step = 8; step > 0; step >>= 1)
+      for (int32_t step = kPiece / 2; step > 0; step >>= 1)
         if (t + step < nnets && s_poff[t + step] <= lo_e) t += step;
       for (; t < nnets && s_poff[t] < hi_e; t++) {
         const int32_t nb = max(lo_e, s_poff[t]), ne = min(hi_e, s_poff[t + 1]);
@@ -1141,11 +1141,11 @@ __global__ void __launch_bounds__(NT) k_gather_w(GatherArgs a) {
         if (whole && !a.summ) {
           g4[x] = b;
         } else {
-          uint32_t *g = a.gbm + slot * a.words + 4 * x;
-          if (b.x) atomicOr(g + 0, b.x);
-          if (b.y) atomicOr(g + 1, b.y);
-          if (b.z) atomicOr(g + 2, b.z);
-          if (b.w) atomicOr(g + 3, b.w);
+          unsigned long long *g = reinterpret_cast<unsigned long long *>(g4 + x);
+          const unsigned long long lo = ((unsigned long long)b.y << 32) | b.x;
+          const unsigned long long hi = ((unsigned long long)b.w << 32) | b.z;
+          if (lo) atomicOr(g + 0, lo);
+          if (hi) atomicOr(g + 1, hi);
         }
         s_bm4[x] = make_uint4(0u, 0u, 0u, 0u);
       }
@@ -1170,11 +1170,17 @@ __global__ void __launch_bounds__(NT) k_gather_w(GatherArgs a) {
           a.gcnt[slot] = 0;
         }
         m = __shfl_sync(kFull, m, 0);
-        for (int32_t x = lane; x < W4; x += 32) {
-          const uint4 q = __ldcg(g4 + x);
-          if (q.x | q.y | q.z | q.w) {
-            s_bm4[x] = q;
-            g4[x] = make_uint4(0u, 0u, 0u, 0u);
+        for (int32_t x0 = lane; x0 < W4; x0 += 128) {  // four loads in flight
+          uint4 q[4];
+#pragma unroll
+          for (int k = 0; k < 4; k++)
+            q[k] = (x0 + 32 * k < W4) ? __ldcg(g4 + x0 + 32 * k) : make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+          for (int k = 0; k < 4; k++) {
+            if (q[k].x | q[k].y | q[k].z | q[k].w) {
+              s_bm4[x0 + 32 * k] = q[k];
+              g4[x0 + 32 * k] = make_uint4(0u, 0u, 0u, 0u);
+            }
           }
         }
         __syncwarp();

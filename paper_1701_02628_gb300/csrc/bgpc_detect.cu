@@ -170,6 +170,95 @@ __global__ void __launch_bounds__(kNT) k_detect_table(const int32_t *__restrict_
   }
 }
 
+// Pair tier, for rounds whose W is small against the graph: the net tiers
+// read every net, while only the (W member, net) pairs can conflict.  Every
+// pair inserts the key (net, color) with its position into an open-addressing
+// hash table that keeps the smallest position per key; then every pair looks
+// its key up, and a member loses when a smaller position holds one of its
+// keys.  The same lose flags as the net tiers, at a cost proportional to the
+// sum over W of |nets(w)|.  Keys never leave the table within a round (it is
+// cleared before the next use), so a probe sequence never breaks.
+constexpr unsigned long long kEmptyKey = ~0ull;
+
+__device__ __forceinline__ unsigned long long pair_key(int32_t v, int32_t c) {
+  return ((unsigned long long)(uint32_t)v << 32) | (uint32_t)c;  // v, c >= 0: never empty
+}
+
+// The splitmix64 output function (a 64-bit mixer with full avalanche).
+__device__ __forceinline__ uint32_t pair_hash(unsigned long long k) {
+  k ^= k >> 30;
+  k *= 0xbf58476d1ce4e5b9ull;
+  k ^= k >> 27;
+  k *= 0x94d049bb133111ebull;
+  k ^= k >> 31;
+  return (uint32_t)k;
+}
+
+__global__ void k_pairs_insert(const int32_t *__restrict__ a_ptr, const int32_t *__restrict__ a_idx,
+                               const int32_t *__restrict__ W, int32_t m,
+                               const int32_t *__restrict__ colors, unsigned long long *keys,
+                               uint32_t *vals, uint32_t mask, int32_t *err) {
+  const int lane = threadIdx.x & 31;
+  int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t p = warp; p < m; p += nwarps) {
+    const int32_t w = W[p];
+    const int32_t c = colors[w];
+    const int32_t beg = a_ptr[w], end = a_ptr[w + 1];
+    for (int32_t i = beg + lane; i < end; i += 32) {
+      const unsigned long long key = pair_key(a_idx[i], c);
+      uint32_t slot = pair_hash(key) & mask;
+      for (uint32_t probe = 0;; probe++) {
+        if (probe > mask) {  // full table: cannot happen at load <= 1/2
+          atomicOr(err, ERR_INTERNAL);
+          break;
+        }
+        unsigned long long k = __ldcg(keys + slot);
+        if (k == kEmptyKey) k = atomicCAS(keys + slot, kEmptyKey, key);
+        if (k == kEmptyKey || k == key) {
+          atomicMin(vals + slot, (uint32_t)p);
+          break;
+        }
+        slot = (slot + 1) & mask;
+      }
+    }
+  }
+}
+
+__global__ void k_pairs_lookup(const int32_t *__restrict__ a_ptr, const int32_t *__restrict__ a_idx,
+                               const int32_t *__restrict__ W, int32_t m,
+                               const int32_t *__restrict__ colors,
+                               const unsigned long long *__restrict__ keys,
+                               const uint32_t *__restrict__ vals, uint32_t mask,
+                               uint8_t *__restrict__ lose, int32_t *err) {
+  const int lane = threadIdx.x & 31;
+  int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t p = warp; p < m; p += nwarps) {
+    const int32_t w = W[p];
+    const int32_t c = colors[w];
+    const int32_t beg = a_ptr[w], end = a_ptr[w + 1];
+    bool l = false;
+    for (int32_t i = beg + lane; i < end && !l; i += 32) {
+      const unsigned long long key = pair_key(a_idx[i], c);
+      uint32_t slot = pair_hash(key) & mask;
+      for (uint32_t probe = 0;; probe++) {
+        const unsigned long long k = keys[slot];
+        if (k == key) {
+          l = vals[slot] < (uint32_t)p;
+          break;
+        }
+        if (k == kEmptyKey || probe > mask) {  // every pair inserted its key
+          atomicOr(err, ERR_INTERNAL);
+          break;
+        }
+        slot = (slot + 1) & mask;
+      }
+    }
+    if (__any_sync(kFull, l) && lane == 0) lose[p] = 1;
+  }
+}
+
 // ----------------------------------------------------------- compaction
 __global__ void __launch_bounds__(kScanNT) k_scan_count(const uint8_t *__restrict__ lose,
                                                         int32_t m, int32_t *__restrict__ blocksum) {
@@ -203,8 +292,11 @@ __global__ void __launch_bounds__(kScanNT) k_scan_scatter(const uint8_t *__restr
                                                           int32_t m,
                                                           const int32_t *__restrict__ blocksum,
                                                           int32_t *__restrict__ newpos,
-                                                          int32_t *__restrict__ Wn) {
+                                                          int32_t *__restrict__ Wn,
+                                                          const int32_t *__restrict__ a_ptr,
+                                                          DevScalars *dev) {
   __shared__ int32_t red[kScanNT / 32];
+  __shared__ unsigned long long s_inc;
   const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanPer;
   int32_t f[kScanPer];
   int32_t c = 0;
@@ -213,16 +305,25 @@ __global__ void __launch_bounds__(kScanNT) k_scan_scatter(const uint8_t *__restr
     f[q] = (base + q < m) ? lose[base + q] : 0;
     c += f[q];
   }
+  if (threadIdx.x == 0) s_inc = 0ull;
   int32_t total;
   int32_t ex = block_excl_scan<kScanNT>(c, red, &total) + blocksum[blockIdx.x];
+  unsigned long long inc = 0ull;  // incidences of the next round's W
 #pragma unroll
   for (int q = 0; q < kScanPer; q++) {
     if (f[q]) {
+      const int32_t w = W[base + q];
       newpos[base + q] = ex;
-      Wn[ex] = W[base + q];
+      Wn[ex] = w;
+      inc += (unsigned long long)(a_ptr[w + 1] - a_ptr[w]);
       ex++;
     }
   }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) inc += __shfl_xor_sync(kFull, inc, o);
+  if ((threadIdx.x & 31) == 0 && inc) atomicAdd(&s_inc, inc);
+  __syncthreads();
+  if (threadIdx.x == 0 && s_inc) atomicAdd(&dev->incid_next, s_inc);
 }
 
 // Losers: uncolored again, and their nc / npos entries carry the new
@@ -311,16 +412,31 @@ int launch_detect(const int32_t *b_ptr, int32_t n_b, const int32_t *nc, const in
   return n;
 }
 
+int launch_detect_pairs(const int32_t *a_ptr, const int32_t *a_idx, const int32_t *W, int32_t m,
+                        const int32_t *colors, unsigned long long *keys, uint32_t *vals,
+                        uint32_t mask, uint8_t *lose, int32_t *err, int sms, cudaStream_t s) {
+  if (m <= 0) return 0;
+  const size_t cap = (size_t)mask + 1;
+  cudaMemsetAsync(keys, 0xff, sizeof(unsigned long long) * cap, s);
+  cudaMemsetAsync(vals, 0xff, sizeof(uint32_t) * cap, s);
+  const int grid = warps_grid(m, sms);
+  k_pairs_insert<<<grid, kNT, 0, s>>>(a_ptr, a_idx, W, m, colors, keys, vals, mask, err);
+  k_pairs_lookup<<<grid, kNT, 0, s>>>(a_ptr, a_idx, W, m, colors, keys, vals, mask, lose, err);
+  return 2;
+}
+
 int launch_compact(const uint8_t *lose, const int32_t *W, int32_t m, int32_t *newpos,
-                    int32_t *Wn, int32_t *blocksum, DevScalars *dev, cudaStream_t s) {
+                    int32_t *Wn, int32_t *blocksum, const int32_t *a_ptr, DevScalars *dev,
+                    cudaStream_t s) {
   const int nblocks = div_up(m, kScanTile);
+  cudaMemsetAsync(&dev->incid_next, 0, sizeof(unsigned long long), s);
   if (m <= 0) {
     cudaMemsetAsync(&dev->m_next, 0, sizeof(int32_t), s);
     return 0;
   }
   k_scan_count<<<nblocks, kScanNT, 0, s>>>(lose, m, blocksum);
   k_scan_blocks<<<1, kScanNT, 0, s>>>(blocksum, nblocks, dev);
-  k_scan_scatter<<<nblocks, kScanNT, 0, s>>>(lose, W, m, blocksum, newpos, Wn);
+  k_scan_scatter<<<nblocks, kScanNT, 0, s>>>(lose, W, m, blocksum, newpos, Wn, a_ptr, dev);
   return 3;
 }
 

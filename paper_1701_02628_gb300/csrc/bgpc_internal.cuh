@@ -38,7 +38,7 @@ constexpr int kSmallWindow = 512;   // bits of the per-vertex small-path window
 constexpr int kSmallD2 = 448;       // small path: sum of net sizes <= this
 constexpr int kSmallMaxDeg = 16;    // small path: at most this many nets
 constexpr int kPairCap = kMaxChunk * kSmallMaxDeg;  // (vertex, net) pairs per chunk
-constexpr int kPiece = 16;          // gather work item: up to this many nets of one vertex
+constexpr int kPiece = 32;          // gather work item: up to this many nets of one vertex
 constexpr int kDetectWarpMax = 32;  // nets up to this size use the warp tier
 // First-fit summary of a large vertex's forbidden set F_S (written by the
 // gather, read by the resolve): the kSumCand smallest free colors, the free
@@ -66,6 +66,7 @@ struct DevScalars {
   unsigned long long trav_hub;   // two-hop entries of hub nets, read as bitmaps instead
   unsigned long long hub_pairs;  // (vertex, hub net) pairs gathered from bitmaps
   unsigned long long acc[4]; // reductions (statistics)
+  unsigned long long incid_next;  // sum over W_{r+1} of |nets(w)| (set by the compaction)
 };
 constexpr int kRoundCounters = 7;  // trav .. hub_pairs, zeroed at the start of a round
 constexpr int32_t kHubMin = 1024;  // a hub net has more members than this and than the
@@ -107,6 +108,8 @@ struct bgpc_ctx {
   size_t h_wlist_cap = 0;
   bgpc::Buf<int32_t> cptr, cidx;       // D2GC closed neighbourhoods
   bgpc::Buf<int32_t> dtab;             // per-slot color tables (detection)
+  bgpc::Buf<unsigned long long> pkeys; // pair-tier detection: (net, color) keys
+  bgpc::Buf<uint32_t> pvals;           // ... and the smallest position per key
   bgpc::Buf<int32_t> vtab;             // per-slot color counts (validation)
   size_t dtab_filled = 0;              // entries of dtab already set to INT_MAX
   bgpc::Buf<unsigned long long> card;  // color-set cardinalities
@@ -249,8 +252,12 @@ int launch_trav(const int32_t *a_ptr, const int32_t *W, const int32_t *d2tot, in
 int launch_detect(const int32_t *b_ptr, int32_t n_b, const int32_t *nc, const int32_t *npos,
                    const int32_t *bigd, int32_t nbigd, int32_t *dtab, int32_t tabcap,
                    int32_t nslots, uint8_t *lose, int sms, cudaStream_t s);
+int launch_detect_pairs(const int32_t *a_ptr, const int32_t *a_idx, const int32_t *W, int32_t m,
+                        const int32_t *colors, unsigned long long *keys, uint32_t *vals,
+                        uint32_t mask, uint8_t *lose, int32_t *err, int sms, cudaStream_t s);
 int launch_compact(const uint8_t *lose, const int32_t *W, int32_t m, int32_t *newpos,
-                    int32_t *Wn, int32_t *blocksum, DevScalars *dev, cudaStream_t s);
+                    int32_t *Wn, int32_t *blocksum, const int32_t *a_ptr, DevScalars *dev,
+                    cudaStream_t s);
 int launch_relabel(const int32_t *a_ptr, const int32_t *tpos, const int32_t *W, int32_t m,
                     uint8_t *lose, const int32_t *newpos, int32_t *nc, int32_t *npos,
                     int32_t *colors, int sms, cudaStream_t s);

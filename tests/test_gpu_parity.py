@@ -36,12 +36,12 @@ def run_gpu(bg, ctx, g, **kw):
     return colors.cpu().numpy(), st, rc, dg
 
 
-def assert_parity(bg, ctx, g, policy=O.FF, chunk=64, waves=16, big_net=64, rank=None):
+def assert_parity(bg, ctx, g, policy=O.FF, chunk=64, waves=16, big_net=64, rank=None, **kw):
     ref = O.rs_color(g, policy, chunk=chunk, waves=waves, big_net=big_net, rank=rank,
                      nthreads=8)
     assert ref.status == O.OK
     got, st, rc, dg = run_gpu(bg, ctx, g, policy=policy, chunk=chunk, waves=waves,
-                              big_net=big_net, rank=rank, validate=True)
+                              big_net=big_net, rank=rank, validate=True, **kw)
     assert rc == bg.BGPC_OK
     bad = np.nonzero(got != ref.colors)[0]
     assert bad.size == 0, f"{bad.size} colors differ, first at {bad[:8]}"
@@ -106,6 +106,21 @@ def test_hub_nets_rank_and_small_chunks(bg, ctx, policy):
     rank = np.random.default_rng(9).permutation(g.n_a).astype(np.int32)
     assert_parity(bg, ctx, g, policy=policy, rank=rank)
     assert_parity(bg, ctx, g, policy=policy, chunk=5, waves=7, big_net=300)
+
+
+@pytest.mark.parametrize("policy", [O.FF, O.B2X])
+@pytest.mark.parametrize("detect", [1, 2, 0])
+def test_detect_tiers(bg, ctx, policy, detect):
+    """Conflict detection after the first round scans every net (1), looks
+    up only the (W member, net) pairs in a hash table (2) or picks one of
+    them by the size of W (0): a mapping choice, the oracle's colors always."""
+    for g in (hub_graph(), gg.chung_lu(20000, 16, 1500, 2.1, seed=4),
+              gg.random_bipartite(3000, 400, 9, seed=6)):
+        assert_parity(bg, ctx, g, policy=policy, detect=detect)
+    g = gg.from_nets(40, [list(range(40))])  # a clique: one round per vertex
+    st = assert_parity(bg, ctx, g, policy=policy, chunk=1, waves=1, big_net=O.NO_BIG,
+                       detect=detect)
+    assert st["rounds"] == 40
 
 
 @pytest.mark.parametrize("chunk,waves,big_net", [(1, 1, O.NO_BIG), (7, 3, 2), (32, 16, 0),
@@ -211,6 +226,10 @@ def test_errors(bg, ctx):
     with pytest.raises(bg.BgpcError) as e:
         bg.bgpc_color(ctx, dg, waves=0)
     assert e.value.status == bg.BGPC_EINVAL
+    for d in (-1, 3):
+        with pytest.raises(bg.BgpcError) as e:
+            bg.bgpc_color(ctx, dg, detect=d)
+        assert e.value.status == bg.BGPC_EINVAL
     bad_rank = torch.zeros(g.n_a, dtype=torch.int32, device="cuda:0")
     with pytest.raises(bg.BgpcError) as e:
         bg.bgpc_color(ctx, dg, rank=bad_rank, validate=True)
