@@ -258,20 +258,38 @@ __device__ __forceinline__ int32_t win_kth_free_down(uint32_t word, int32_t top,
 // the summary only when its chunk-mates take all kCand.
 constexpr int kCand = 32;
 
-// The N smallest colors not in g, ascending, into out[].
+// The N smallest colors not in g, ascending, into out[].  g holds `words`
+// words (16-byte aligned, words a multiple of 4; colors beyond are free);
+// each lane takes four words per step.
+template <int N>
+__device__ __forceinline__ void take_up(uint32_t fr, int32_t base, int32_t &r, int32_t *out) {
+  while (fr && r < N) {
+    out[r++] = base + __ffs(fr) - 1;
+    fr &= fr - 1u;
+  }
+}
+
 template <int N>
 __device__ __forceinline__ void warp_first_free(const uint32_t *g, int32_t words, int32_t *out) {
   const int lane = threadIdx.x & 31;
+  const uint4 *g4 = reinterpret_cast<const uint4 *>(g);
+  const int32_t W4 = words >> 2;
   int32_t got = 0;
-  for (int32_t w0 = 0; got < N; w0 += 32) {
-    const int32_t wi = w0 + lane;
-    uint32_t fr = (wi < words) ? ~g[wi] : 0xffffffffu;
-    const int32_t cnt = __popc(fr);
+  for (int32_t q0 = 0; got < N; q0 += 32) {
+    const int32_t q = q0 + lane;
+    uint4 f = make_uint4(0xffffffffu, 0xffffffffu, 0xffffffffu, 0xffffffffu);
+    if (q < W4) {
+      const uint4 b = g4[q];
+      f = make_uint4(~b.x, ~b.y, ~b.z, ~b.w);
+    }
+    const int32_t cnt = __popc(f.x) + __popc(f.y) + __popc(f.z) + __popc(f.w);
     const int32_t inc = warp_incl_scan(cnt);
     int32_t r = got + inc - cnt;
-    while (fr && r < N) {
-      out[r++] = wi * 32 + __ffs(fr) - 1;
-      fr &= fr - 1u;
+    if (r < N) {
+      take_up<N>(f.x, 128 * q, r, out);
+      take_up<N>(f.y, 128 * q + 32, r, out);
+      take_up<N>(f.z, 128 * q + 64, r, out);
+      take_up<N>(f.w, 128 * q + 96, r, out);
     }
     got += __shfl_sync(kFull, inc, 31);
   }
@@ -280,30 +298,46 @@ __device__ __forceinline__ void warp_first_free(const uint32_t *g, int32_t words
 
 // Colors not in g counted down from top: the k-th .. (k+N-1)-th (0-based)
 // into out[], descending.  Returns how many of them exist (0 if fewer than
-// k + 1 free colors lie in [0, top]).
+// k + 1 free colors lie in [0, top]).  g as above, top < 32 * words; each lane
+// takes four words per step, lane 0 the highest.
 template <int N>
-__device__ __forceinline__ int32_t warp_kth_free_down(const uint32_t *g, int32_t words,
-                                                      int32_t top, int32_t k, int32_t *out) {
+__device__ __forceinline__ void take_down(uint32_t fr, int32_t base, int32_t k, int32_t &r,
+                                          int32_t *out) {
+  const int32_t c = __popc(fr);
+  if (r + c <= k) {  // the whole word lies before the k-th
+    r += c;
+    return;
+  }
+  while (fr && r < k + N) {
+    const int32_t b = 31 - __clz(fr);
+    if (r >= k) out[r - k] = base + b;
+    r++;
+    fr &= ~(1u << b);
+  }
+}
+
+template <int N>
+__device__ __forceinline__ int32_t warp_kth_free_down(const uint32_t *g, int32_t top, int32_t k,
+                                                      int32_t *out) {
   const int lane = threadIdx.x & 31;
+  const uint4 *g4 = reinterpret_cast<const uint4 *>(g);
   int32_t seen = 0;
-  const int32_t wtop = top >> 5;
-  for (int32_t w0 = wtop; w0 >= 0 && seen < k + N; w0 -= 32) {
-    const int32_t wi = w0 - lane;  // lane 0 holds the highest word
-    uint32_t fr = 0u;
-    if (wi >= 0) {
-      fr = (wi < words) ? ~g[wi] : 0xffffffffu;
-      if (wi == wtop) fr &= mask_upto(wi * 32, top);
+  for (int32_t q0 = top >> 7; q0 >= 0 && seen < k + N; q0 -= 32) {
+    const int32_t q = q0 - lane;
+    uint4 f = make_uint4(0u, 0u, 0u, 0u);
+    if (q >= 0) {
+      const uint4 b = g4[q];
+      f = make_uint4(~b.x & mask_upto(128 * q, top), ~b.y & mask_upto(128 * q + 32, top),
+                     ~b.z & mask_upto(128 * q + 64, top), ~b.w & mask_upto(128 * q + 96, top));
     }
-    const int32_t cnt = __popc(fr);
+    const int32_t cnt = __popc(f.x) + __popc(f.y) + __popc(f.z) + __popc(f.w);
     const int32_t inc = warp_incl_scan(cnt);
     int32_t r = seen + inc - cnt;  // rank of this lane's highest free color
     if (r + cnt > k && r < k + N) {
-      while (fr && r < k + N) {
-        const int32_t b = 31 - __clz(fr);
-        if (r >= k) out[r - k] = wi * 32 + b;
-        r++;
-        fr &= ~(1u << b);
-      }
+      take_down<N>(f.w, 128 * q + 96, k, r, out);
+      take_down<N>(f.z, 128 * q + 64, k, r, out);
+      take_down<N>(f.y, 128 * q + 32, k, r, out);
+      take_down<N>(f.x, 128 * q, k, r, out);
     }
     seen += __shfl_sync(kFull, inc, 31);
   }
@@ -322,16 +356,17 @@ __device__ __forceinline__ void warp_summarize(const uint32_t *bm, int32_t words
   const int lane = threadIdx.x & 31;
   warp_first_free<kSumCand>(bm, words, rec);
   int32_t rc = 0;
-  if (so > T) rc = warp_kth_free_down<kSumCand>(bm, words, so - 1, k, rec + kSumCand);
+  if (so > T) rc = warp_kth_free_down<kSumCand>(bm, so - 1, k, rec + kSumCand);
   if (lane == 0) {
     rec[2 * kSumCand] = rc;
     *reinterpret_cast<unsigned long long *>(rec + 2 * kSumCand + 2) = adj;
   }
   if (rc > 0) {
-    const int32_t n4 = min(words >> 2, ((so - 1) >> 7) + 1);
+    // the resolve tests overlay colors in (ak, so - 1] only, ak = the k-th
+    const int32_t ak = rec[kSumCand];
     const uint4 *b4 = reinterpret_cast<const uint4 *>(bm);
     uint4 *l4 = reinterpret_cast<uint4 *>(lb);
-    for (int32_t x = lane; x < n4; x += 32) l4[x] = b4[x];
+    for (int32_t x = (ak >> 7) + lane; x <= ((so - 1) >> 7); x += 32) l4[x] = b4[x];
   }
   __syncwarp();
 }
@@ -817,6 +852,33 @@ __device__ __forceinline__ int32_t lower_bound(const int32_t *__restrict__ l, in
   return lo;
 }
 
+// Two lower bounds in the sorted list l[0, n) at once, by one warp: lanes
+// 0-15 search key0, lanes 16-31 key1, each half probing 16 evenly spaced
+// entries per round (the range shrinks 16-fold per dependent load instead of
+// 2-fold).  Returns (lower_bound(key0), lower_bound(key1)) in every lane.
+__device__ __forceinline__ int2 warp_lower_bounds(const int32_t *__restrict__ l, int32_t n,
+                                                  int32_t key0, int32_t key1) {
+  const int lane = threadIdx.x & 31;
+  const int sl = lane & 15;
+  const unsigned half = (lane < 16) ? 0x0000ffffu : 0xffff0000u;
+  const int32_t key = (lane < 16) ? key0 : key1;
+  int32_t lo = 0, hi = n;  // the answer lies in [lo, hi]
+  while (__any_sync(kFull, lo < hi)) {
+    const int32_t step = (hi - lo + 15) >> 4;
+    const int32_t e = lo + (sl + 1) * step - 1;  // last entry of sub-range sl
+    const bool valid = lo < hi && e < hi;
+    const bool below = valid && __ldg(l + e) < key;
+    const int32_t cnt = __popc(__ballot_sync(kFull, below) & half);
+    const int32_t ec = lo + (cnt + 1) * step - 1;
+    if (lo < hi) {
+      const int32_t nlo = lo + cnt * step;
+      hi = (cnt < 16 && ec < hi) ? ec : hi;
+      lo = nlo;
+    }
+  }
+  return make_int2(__shfl_sync(kFull, lo, 0), __shfl_sync(kFull, lo, 16));
+}
+
 // Whether vertex u is in the sorted list l[0, n).
 __device__ __forceinline__ bool sorted_has(const int32_t *__restrict__ l, int32_t n, int32_t u) {
   const int32_t lo = lower_bound(l, n, u);
@@ -912,9 +974,8 @@ __global__ void __launch_bounds__(NT) k_gather(GatherArgs a) {
         const int32_t id_lo = a.W[p0], id_hi = a.W[p0 + rel_hi - 1];
         for (int32_t h = warp; h < nh; h += NW) {
           const int32_t *l = a.b_idx + s_hbp[h];
-          int32_t b = 0;
-          if (lane < 2) b = lower_bound(l, s_hsz[h], lane == 0 ? id_lo : id_hi + 1);
-          const int32_t lb = __shfl_sync(kFull, b, 0), ub = __shfl_sync(kFull, b, 1);
+          const int2 bb = warp_lower_bounds(l, s_hsz[h], id_lo, id_hi + 1);
+          const int32_t lb = bb.x, ub = bb.y;
           for (int32_t f = lb + lane; f < ub; f += 32) {
             const int32_t x = a.nc[s_hbp[h] + f];
             const int32_t rel = (-2 - x) - p0;
@@ -1028,7 +1089,7 @@ __device__ __forceinline__ void warp_clear(uint4 *bm4, int32_t n4) {
 // other warps' streaming.  Same results as k_gather: the bitmap and mask of
 // a piece are ORed into the vertex's slot the same way.
 template <int NT>
-__global__ void __launch_bounds__(NT) k_gather_w(GatherArgs a) {
+__global__ void __launch_bounds__(NT, 4) k_gather_w(GatherArgs a) {
   constexpr int NW = NT / 32;
   extern __shared__ __align__(16) uint32_t s_all[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -1098,9 +1159,8 @@ __global__ void __launch_bounds__(NT) k_gather_w(GatherArgs a) {
         if (rel_hi > 0) {
           const int32_t *l = a.b_idx + hbp;
           if (a.id_order) {
-            int32_t b = 0;
-            if (lane < 2) b = lower_bound(l, hsz, lane == 0 ? id_lo : id_hi + 1);
-            const int32_t lb = __shfl_sync(kFull, b, 0), ub = __shfl_sync(kFull, b, 1);
+            const int2 bb = warp_lower_bounds(l, hsz, id_lo, id_hi + 1);
+            const int32_t lb = bb.x, ub = bb.y;
             for (int32_t f = lb + lane; f < ub; f += 32) {
               const int32_t x = a.nc[hbp + f];
               const int32_t rel = (-2 - x) - p0;
@@ -1114,11 +1174,35 @@ __global__ void __launch_bounds__(NT) k_gather_w(GatherArgs a) {
       }
       __syncwarp();
     }
-    // ---- the other nets: stream their mirror words
-    for (int t = 0; t < nnets; t++) {
-      const int32_t n = __shfl_sync(kFull, hub >= 0 ? 0 : sz, t);
-      const int32_t b = __shfl_sync(kFull, bp, t);
-      if (n > 0) warp_stream(a.nc + b, n, s_bm, lim, p0, rel_hi, adj);
+    // ---- the other nets: those of up to 64 members four at a time (two
+    // words per lane each, eight loads in flight), larger ones streamed
+    unsigned few = __ballot_sync(kFull, hub < 0 && sz > 0 && sz <= 64);
+    const unsigned lg = __ballot_sync(kFull, hub < 0 && sz > 64);
+    while (few) {
+      int32_t n[4], b[4];
+#pragma unroll
+      for (int k = 0; k < 4; k++) {
+        const int t = few ? __ffs(few) - 1 : 0;
+        n[k] = few ? __shfl_sync(kFull, sz, t) : 0;
+        b[k] = __shfl_sync(kFull, bp, t);
+        few &= few - 1u;
+      }
+      int32_t x[8];
+#pragma unroll
+      for (int k = 0; k < 4; k++) {
+        x[2 * k] = (lane < n[k]) ? __ldg(a.nc + b[k] + lane) : 0;
+        x[2 * k + 1] = (lane + 32 < n[k]) ? __ldg(a.nc + b[k] + lane + 32) : 0;
+      }
+#pragma unroll
+      for (int k = 0; k < 4; k++) {
+        if (lane < n[k]) take(x[2 * k], s_bm, lim, p0, rel_hi, adj);
+        if (lane + 32 < n[k]) take(x[2 * k + 1], s_bm, lim, p0, rel_hi, adj);
+      }
+    }
+    for (unsigned m = lg; m; m &= m - 1u) {
+      const int t = __ffs(m) - 1;
+      warp_stream(a.nc + __shfl_sync(kFull, bp, t), __shfl_sync(kFull, sz, t), s_bm, lim, p0,
+                  rel_hi, adj);
     }
     const unsigned lo32 = __reduce_or_sync(kFull, (unsigned)(adj & 0xffffffffull));
     const unsigned hi32 = __reduce_or_sync(kFull, (unsigned)(adj >> 32));
