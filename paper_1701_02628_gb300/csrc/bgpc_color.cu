@@ -1131,32 +1131,49 @@ __global__ void __launch_bounds__(NT, 4) k_gather_w(GatherArgs a) {
         id_lo = a.W[p0];
         id_hi = a.W[p0 + rel_hi - 1];
       }
-      for (unsigned hm = hubs; hm; hm &= hm - 1u) {
-        const int t = __ffs(hm) - 1;
-        const int32_t slot = __shfl_sync(kFull, hub, t);
-        const int32_t hbp = __shfl_sync(kFull, bp, t), hsz = __shfl_sync(kFull, sz, t);
-        // the hub's colors: each lane ORs its own 16-byte words, four
-        // loads in flight
-        const uint4 *src = nb4 + (int64_t)slot * W4;
-        for (int32_t x0 = lane; x0 < W4; x0 += 128) {
-          uint4 q[4];
-#pragma unroll
-          for (int k = 0; k < 4; k++)
-            q[k] = (x0 + 32 * k < W4) ? __ldg(src + x0 + 32 * k) : make_uint4(0u, 0u, 0u, 0u);
-#pragma unroll
-          for (int k = 0; k < 4; k++) {
-            if (q[k].x | q[k].y | q[k].z | q[k].w) {
-              uint4 c = s_bm4[x0 + 32 * k];
-              c.x |= q[k].x;
-              c.y |= q[k].y;
-              c.z |= q[k].z;
-              c.w |= q[k].w;
-              s_bm4[x0 + 32 * k] = c;
-            }
+      // the hubs' colors: each lane ORs its own 16-byte words of every hub
+      // (two words of two hubs per step, four loads in flight) and updates
+      // the bitmap once per word
+      // (the loop bounds are the same in every lane: the shuffles below
+      // need the whole warp)
+      const uint4 zero = make_uint4(0u, 0u, 0u, 0u);
+      for (int32_t xb = 0; xb < W4; xb += 64) {
+        const int32_t x0 = xb + lane;
+        const bool v0 = x0 < W4, v1 = x0 + 32 < W4;
+        uint4 c0 = zero, c1 = zero;
+        for (unsigned hm = hubs; hm;) {
+          const int32_t s0 = __shfl_sync(kFull, hub, __ffs(hm) - 1);
+          hm &= hm - 1u;
+          const int32_t s1 = hm ? __shfl_sync(kFull, hub, __ffs(hm) - 1) : -1;
+          hm &= hm - 1u;
+          const uint4 *h0 = nb4 + (int64_t)s0 * W4 + x0;
+          const uint4 q00 = v0 ? __ldg(h0) : zero;
+          const uint4 q01 = v1 ? __ldg(h0 + 32) : zero;
+          uint4 q10 = zero, q11 = zero;
+          if (s1 >= 0) {
+            const uint4 *h1 = nb4 + (int64_t)s1 * W4 + x0;
+            q10 = v0 ? __ldg(h1) : zero;
+            q11 = v1 ? __ldg(h1 + 32) : zero;
           }
+          c0 = make_uint4(c0.x | q00.x | q10.x, c0.y | q00.y | q10.y, c0.z | q00.z | q10.z,
+                          c0.w | q00.w | q10.w);
+          c1 = make_uint4(c1.x | q01.x | q11.x, c1.y | q01.y | q11.y, c1.z | q01.z | q11.z,
+                          c1.w | q01.w | q11.w);
         }
-        // its earlier chunk-mates
-        if (rel_hi > 0) {
+        if (v0 && (c0.x | c0.y | c0.z | c0.w)) {
+          const uint4 b = s_bm4[x0];
+          s_bm4[x0] = make_uint4(b.x | c0.x, b.y | c0.y, b.z | c0.z, b.w | c0.w);
+        }
+        if (c1.x | c1.y | c1.z | c1.w) {
+          const uint4 b = s_bm4[x0 + 32];
+          s_bm4[x0 + 32] = make_uint4(b.x | c1.x, b.y | c1.y, b.z | c1.z, b.w | c1.w);
+        }
+      }
+      // their earlier chunk-mates
+      for (unsigned hm = hubs; hm && rel_hi > 0; hm &= hm - 1u) {
+        const int t = __ffs(hm) - 1;
+        const int32_t hbp = __shfl_sync(kFull, bp, t), hsz = __shfl_sync(kFull, sz, t);
+        {
           const int32_t *l = a.b_idx + hbp;
           if (a.id_order) {
             const int2 bb = warp_lower_bounds(l, hsz, id_lo, id_hi + 1);
