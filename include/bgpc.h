@@ -135,7 +135,8 @@ typedef struct {
     int64_t trav_hub;    /* all rounds: the part of trav_large in hub nets (more than 1024
                             members), read from per-net color bitmaps instead of streamed */
     int64_t hub_pairs;   /* all rounds: (vertex, hub net) pairs so read */
-    int64_t hub_words;   /* all rounds: bitmap words so read (hub_pairs x the round's width) */
+    int64_t hub_words;   /* all rounds: bitmap words so read (under first fit a one-piece
+                            vertex reads only the words its summary needs) */
 } bgpc_stats_t;
 
 /* Fill `opts` with the defaults: FF, C=64, Q=16, T=64, id order,

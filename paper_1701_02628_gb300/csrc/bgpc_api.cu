@@ -186,7 +186,7 @@ int color_impl(bgpc_ctx_t *ctx, const bgpc_graph_t &g, const bgpc_opts_t &o, int
   nk += launch_net_static(g, o.big_net, ctx->bigt.p, ctx->bigd.p, ctx->dev, s);
   nk += launch_hub_select(g.b_ptr, n_b, kHubMin, ctx->hub_id.p, ctx->hub_net.p, ctx->dev, sms, s);
   nk += launch_init_queue(o.rank, n_a, ctx->W0.p, &ctx->dev->err, s);
-  nk += launch_init_mirror(g, o.rank, ctx->tpos.p, ctx->nc.p, ctx->npos.p, colors, sms, s);
+  nk += launch_init_mirror(g, o.rank, ctx->nc.p, ctx->npos.p, colors, sms, s);
   tm.end(ev, PH_SETUP);
   CU(cudaGetLastError());
   if ((rc = sync_scalars(ctx, s))) return rc;
@@ -307,6 +307,7 @@ int color_impl(bgpc_ctx_t *ctx, const bgpc_graph_t &g, const bgpc_opts_t &o, int
         ga.gbm = ctx->gbm.p;
         ga.gadj = ctx->gadj.p;
         ga.b_idx = g.b_idx;
+        ga.tpos = ctx->tpos.p;
         ga.hub_id = nhub > 0 ? ctx->hub_id.p : nullptr;
         ga.nbm = ctx->nbm.p;
         ga.dev = ctx->dev;
@@ -412,7 +413,7 @@ int color_impl(bgpc_ctx_t *ctx, const bgpc_graph_t &g, const bgpc_opts_t &o, int
     st.w_large += (int64_t)ctx->host->w_large;
     st.trav_hub += (int64_t)ctx->host->trav_hub;
     st.hub_pairs += (int64_t)ctx->host->hub_pairs;
-    st.hub_words += (int64_t)ctx->host->hub_pairs * words;
+    st.hub_words += (int64_t)ctx->host->hub_words;
     st.pieces_total += ctx->host->nseg;
     st.w_total += m;
     r++;

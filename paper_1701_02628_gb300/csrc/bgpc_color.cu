@@ -269,18 +269,23 @@ __device__ __forceinline__ void take_up(uint32_t fr, int32_t base, int32_t &r, i
   }
 }
 
+// Resumable: scans the 16-byte groups from q0 on while fewer than N colors
+// are found and q0 < qend (groups at or beyond qend are not read: a caller
+// may not have finished them); groups at or beyond W4 are all free.
 template <int N>
-__device__ __forceinline__ void warp_first_free(const uint32_t *g, int32_t words, int32_t *out) {
+__device__ __forceinline__ void warp_first_free_from(const uint32_t *g, int32_t W4, int32_t qend,
+                                                     int32_t *out, int32_t &got, int32_t &q0) {
   const int lane = threadIdx.x & 31;
   const uint4 *g4 = reinterpret_cast<const uint4 *>(g);
-  const int32_t W4 = words >> 2;
-  int32_t got = 0;
-  for (int32_t q0 = 0; got < N; q0 += 32) {
+  while (got < N && q0 < qend) {
     const int32_t q = q0 + lane;
-    uint4 f = make_uint4(0xffffffffu, 0xffffffffu, 0xffffffffu, 0xffffffffu);
-    if (q < W4) {
-      const uint4 b = g4[q];
-      f = make_uint4(~b.x, ~b.y, ~b.z, ~b.w);
+    uint4 f = make_uint4(0u, 0u, 0u, 0u);
+    if (q < qend) {
+      f = make_uint4(0xffffffffu, 0xffffffffu, 0xffffffffu, 0xffffffffu);
+      if (q < W4) {
+        const uint4 b = g4[q];
+        f = make_uint4(~b.x, ~b.y, ~b.z, ~b.w);
+      }
     }
     const int32_t cnt = __popc(f.x) + __popc(f.y) + __popc(f.z) + __popc(f.w);
     const int32_t inc = warp_incl_scan(cnt);
@@ -292,14 +297,17 @@ __device__ __forceinline__ void warp_first_free(const uint32_t *g, int32_t words
       take_up<N>(f.w, 128 * q + 96, r, out);
     }
     got += __shfl_sync(kFull, inc, 31);
+    q0 = (qend - q0 > 32) ? q0 + 32 : qend;
   }
   __syncwarp();
 }
 
-// Colors not in g counted down from top: the k-th .. (k+N-1)-th (0-based)
-// into out[], descending.  Returns how many of them exist (0 if fewer than
-// k + 1 free colors lie in [0, top]).  g as above, top < 32 * words; each lane
-// takes four words per step, lane 0 the highest.
+template <int N>
+__device__ __forceinline__ void warp_first_free(const uint32_t *g, int32_t words, int32_t *out) {
+  int32_t got = 0, q0 = 0;
+  warp_first_free_from<N>(g, words >> 2, INT32_MAX, out, got, q0);
+}
+
 template <int N>
 __device__ __forceinline__ void take_down(uint32_t fr, int32_t base, int32_t k, int32_t &r,
                                           int32_t *out) {
@@ -350,11 +358,12 @@ __device__ __forceinline__ int32_t warp_kth_free_down(const uint32_t *g, int32_t
 // bitmap bm (`words` words, read only) into rec[kSumInts]; the owner of a net
 // larger than T (so > T) with a k-th free color also leaves the bitmap words
 // up to color so - 1 in lb, for the resolve's tests of overlay colors.
-__device__ __forceinline__ void warp_summarize(const uint32_t *bm, int32_t words, int32_t so,
-                                               int32_t T, int32_t k, unsigned long long adj,
-                                               int32_t *rec, uint32_t *lb) {
+// The summary's reverse first-fit part, count and mask (its first-fit list
+// already in rec[0, kSumCand)).
+__device__ __forceinline__ void warp_summarize_rest(const uint32_t *bm, int32_t so, int32_t T,
+                                                    int32_t k, unsigned long long adj,
+                                                    int32_t *rec, uint32_t *lb) {
   const int lane = threadIdx.x & 31;
-  warp_first_free<kSumCand>(bm, words, rec);
   int32_t rc = 0;
   if (so > T) rc = warp_kth_free_down<kSumCand>(bm, so - 1, k, rec + kSumCand);
   if (lane == 0) {
@@ -369,6 +378,13 @@ __device__ __forceinline__ void warp_summarize(const uint32_t *bm, int32_t words
     for (int32_t x = (ak >> 7) + lane; x <= ((so - 1) >> 7); x += 32) l4[x] = b4[x];
   }
   __syncwarp();
+}
+
+__device__ __forceinline__ void warp_summarize(const uint32_t *bm, int32_t words, int32_t so,
+                                               int32_t T, int32_t k, unsigned long long adj,
+                                               int32_t *rec, uint32_t *lb) {
+  warp_first_free<kSumCand>(bm, words, rec);
+  warp_summarize_rest(bm, so, T, k, adj, rec, lb);
 }
 
 // Index of the candidate equal to c in a sorted list (ascending if asc),
@@ -936,6 +952,7 @@ __global__ void __launch_bounds__(NT) k_gather(GatherArgs a) {
         if (lane == 0) {
           atomicAdd(&a.dev->trav_hub, (unsigned long long)hv);
           atomicAdd(&a.dev->hub_pairs, (unsigned long long)__popc(hubs));
+          atomicAdd(&a.dev->hub_words, (unsigned long long)__popc(hubs) * a.words);
         }
       }
       if (lane == 0) {
@@ -1083,6 +1100,51 @@ __device__ __forceinline__ void warp_clear(uint4 *bm4, int32_t n4) {
   __syncwarp();
 }
 
+// The hubs' colors into a warp's bitmap, 16-byte groups [qlo, qhi): each
+// lane ORs its own groups of every hub of the piece (two groups of two hubs
+// per step, four loads in flight) and updates the bitmap once per group.
+// hubs = the lanes whose net is a hub, hub = this lane's hub slot.  The loop
+// bounds are the same in every lane: the shuffles need the whole warp.
+__device__ __forceinline__ void warp_hub_or(uint4 *s_bm4, const uint4 *nb4, int32_t W4,
+                                            unsigned hubs, int32_t hub, int32_t qlo,
+                                            int32_t qhi) {
+  const int lane = threadIdx.x & 31;
+  const uint4 zero = make_uint4(0u, 0u, 0u, 0u);
+  for (int32_t xb = qlo; xb < qhi; xb += 64) {
+    const int32_t x0 = xb + lane;
+    const bool v0 = x0 < qhi, v1 = x0 + 32 < qhi;
+    uint4 c0 = zero, c1 = zero;
+    for (unsigned hm = hubs; hm;) {
+      const int32_t s0 = __shfl_sync(kFull, hub, __ffs(hm) - 1);
+      hm &= hm - 1u;
+      const int32_t s1 = hm ? __shfl_sync(kFull, hub, __ffs(hm) - 1) : -1;
+      hm &= hm - 1u;
+      const uint4 *h0 = nb4 + (int64_t)s0 * W4 + x0;
+      const uint4 q00 = v0 ? __ldg(h0) : zero;
+      const uint4 q01 = v1 ? __ldg(h0 + 32) : zero;
+      uint4 q10 = zero, q11 = zero;
+      if (s1 >= 0) {
+        const uint4 *h1 = nb4 + (int64_t)s1 * W4 + x0;
+        q10 = v0 ? __ldg(h1) : zero;
+        q11 = v1 ? __ldg(h1 + 32) : zero;
+      }
+      c0 = make_uint4(c0.x | q00.x | q10.x, c0.y | q00.y | q10.y, c0.z | q00.z | q10.z,
+                      c0.w | q00.w | q10.w);
+      c1 = make_uint4(c1.x | q01.x | q11.x, c1.y | q01.y | q11.y, c1.z | q01.z | q11.z,
+                      c1.w | q01.w | q11.w);
+    }
+    if (v0 && (c0.x | c0.y | c0.z | c0.w)) {
+      const uint4 b = s_bm4[x0];
+      s_bm4[x0] = make_uint4(b.x | c0.x, b.y | c0.y, b.z | c0.z, b.w | c0.w);
+    }
+    if (c1.x | c1.y | c1.z | c1.w) {
+      const uint4 b = s_bm4[x0 + 32];
+      s_bm4[x0 + 32] = make_uint4(b.x | c1.x, b.y | c1.y, b.z | c1.z, b.w | c1.w);
+    }
+  }
+  __syncwarp();
+}
+
 // Warp-private form of the gather: every warp takes whole pieces on its own,
 // with its own bitmap in shared memory, so no CTA barrier stands between a
 // piece's dependent loads (piece -> vertex -> nets -> net extents) and the
@@ -1101,6 +1163,7 @@ __global__ void __launch_bounds__(NT, 4) k_gather_w(GatherArgs a) {
   const int32_t sbeg = a.segoff[a.slot_lo], send = a.segoff[a.slot_hi];
   const uint4 *nb4 = reinterpret_cast<const uint4 *>(a.nbm);
   const int64_t nwarps = (int64_t)gridDim.x * NW;
+  unsigned long long n_trav_hub = 0, n_hub_pairs = 0, n_hub_groups = 0;  // lane 0's counts
   for (int64_t sg = sbeg + (int64_t)blockIdx.x * NW + warp; sg < send; sg += nwarps) {
     // ---- the piece: its vertex, its chunk and its nets (one net per lane)
     const int2 sm = a.segmap[sg];
@@ -1111,82 +1174,55 @@ __global__ void __launch_bounds__(NT, 4) k_gather_w(GatherArgs a) {
     const int32_t ibeg = a.a_ptr[w] + piece * kPiece;
     const int32_t nnets = min(a.a_ptr[w + 1] - ibeg, kPiece);
     const bool whole = (a.segoff[u + 1] - a.segoff[u]) == 1;
-    int32_t sz = 0, bp = 0, hub = -1;
+    int32_t sz = 0, bp = 0, hub = -1, tp = 0;
     if (lane < nnets) {
       const int32_t v = a.a_idx[ibeg + lane];
       bp = a.b_ptr[v];
       sz = a.b_ptr[v + 1] - bp;
       hub = a.hub_id ? a.hub_id[v] : -1;
+      if (a.id_order && hub >= 0) tp = a.tpos[ibeg + lane];
     }
     const unsigned hubs = __ballot_sync(kFull, hub >= 0);
     unsigned long long adj = 0ull;
+    // hub groups ORed here: all of them, except for a one-piece first-fit
+    // vertex, whose summary reads the groups up to its owner's top s - 1
+    // (and more only if its first 64 free colors lie beyond them)
+    int32_t so = 0, qor = W4;
+    if (a.summ && whole) {
+      so = a.s_own[w];
+      qor = min(W4, max(so > a.T ? ((so - 1) >> 7) + 1 : 0, 2));
+    }
     if (hubs) {
-      const int32_t hv = __reduce_add_sync(kFull, hub >= 0 ? sz - 1 : 0);
-      if (lane == 0) {
-        atomicAdd(&a.dev->trav_hub, (unsigned long long)hv);
-        atomicAdd(&a.dev->hub_pairs, (unsigned long long)__popc(hubs));
-      }
+      n_trav_hub += (unsigned long long)__reduce_add_sync(kFull, hub >= 0 ? sz - 1 : 0);
+      n_hub_pairs += (unsigned long long)__popc(hubs);
+      n_hub_groups += (unsigned long long)__popc(hubs) * qor;
       int32_t id_lo = 0, id_hi = 0;
       if (a.id_order && rel_hi > 0) {
         id_lo = a.W[p0];
         id_hi = a.W[p0 + rel_hi - 1];
       }
-      // the hubs' colors: each lane ORs its own 16-byte words of every hub
-      // (two words of two hubs per step, four loads in flight) and updates
-      // the bitmap once per word
-      // (the loop bounds are the same in every lane: the shuffles below
-      // need the whole warp)
-      const uint4 zero = make_uint4(0u, 0u, 0u, 0u);
-      for (int32_t xb = 0; xb < W4; xb += 64) {
-        const int32_t x0 = xb + lane;
-        const bool v0 = x0 < W4, v1 = x0 + 32 < W4;
-        uint4 c0 = zero, c1 = zero;
-        for (unsigned hm = hubs; hm;) {
-          const int32_t s0 = __shfl_sync(kFull, hub, __ffs(hm) - 1);
-          hm &= hm - 1u;
-          const int32_t s1 = hm ? __shfl_sync(kFull, hub, __ffs(hm) - 1) : -1;
-          hm &= hm - 1u;
-          const uint4 *h0 = nb4 + (int64_t)s0 * W4 + x0;
-          const uint4 q00 = v0 ? __ldg(h0) : zero;
-          const uint4 q01 = v1 ? __ldg(h0 + 32) : zero;
-          uint4 q10 = zero, q11 = zero;
-          if (s1 >= 0) {
-            const uint4 *h1 = nb4 + (int64_t)s1 * W4 + x0;
-            q10 = v0 ? __ldg(h1) : zero;
-            q11 = v1 ? __ldg(h1 + 32) : zero;
-          }
-          c0 = make_uint4(c0.x | q00.x | q10.x, c0.y | q00.y | q10.y, c0.z | q00.z | q10.z,
-                          c0.w | q00.w | q10.w);
-          c1 = make_uint4(c1.x | q01.x | q11.x, c1.y | q01.y | q11.y, c1.z | q01.z | q11.z,
-                          c1.w | q01.w | q11.w);
-        }
-        if (v0 && (c0.x | c0.y | c0.z | c0.w)) {
-          const uint4 b = s_bm4[x0];
-          s_bm4[x0] = make_uint4(b.x | c0.x, b.y | c0.y, b.z | c0.z, b.w | c0.w);
-        }
-        if (c1.x | c1.y | c1.z | c1.w) {
-          const uint4 b = s_bm4[x0 + 32];
-          s_bm4[x0 + 32] = make_uint4(b.x | c1.x, b.y | c1.y, b.z | c1.z, b.w | c1.w);
-        }
-      }
-      // their earlier chunk-mates
+      warp_hub_or(s_bm4, nb4, W4, hubs, hub, 0, qor);
+      // their earlier chunk-mates.  In id order a chunk's earlier vertices
+      // have ids in [id_lo, w), so in the id-sorted vtxs(v) they sit right
+      // before w's own entry (its CSC index tp): read backwards from there
+      // while the ids stay >= id_lo (one window of 32 per step, usually one
+      // step); the mirror words of those entries carry the queue positions.
       for (unsigned hm = hubs; hm && rel_hi > 0; hm &= hm - 1u) {
         const int t = __ffs(hm) - 1;
         const int32_t hbp = __shfl_sync(kFull, bp, t), hsz = __shfl_sync(kFull, sz, t);
-        {
-          const int32_t *l = a.b_idx + hbp;
-          if (a.id_order) {
-            const int2 bb = warp_lower_bounds(l, hsz, id_lo, id_hi + 1);
-            const int32_t lb = bb.x, ub = bb.y;
-            for (int32_t f = lb + lane; f < ub; f += 32) {
-              const int32_t x = a.nc[hbp + f];
-              const int32_t rel = (-2 - x) - p0;
-              if (x < 0 && rel >= 0 && rel < rel_hi) adj |= 1ull << rel;
-            }
-          } else {
-            for (int32_t jj = lane; jj < rel_hi; jj += 32)
-              if (sorted_has(l, hsz, a.W[p0 + jj])) adj |= 1ull << jj;
+        if (a.id_order) {
+          for (int32_t top = __shfl_sync(kFull, tp, t) - 1;; top -= 32) {
+            const int32_t f = top - lane;
+            const bool in = f >= hbp && __ldg(a.b_idx + f) >= id_lo;
+            const int32_t x = in ? a.nc[f] : 0;
+            const int32_t rel = (-2 - x) - p0;
+            if (in && x < 0 && rel >= 0 && rel < rel_hi) adj |= 1ull << rel;
+            if (__ballot_sync(kFull, in) != kFull) break;
           }
+        } else {
+          const int32_t *l = a.b_idx + hbp;
+          for (int32_t jj = lane; jj < rel_hi; jj += 32)
+            if (sorted_has(l, hsz, a.W[p0 + jj])) adj |= 1ull << jj;
         }
       }
       __syncwarp();
@@ -1228,9 +1264,18 @@ __global__ void __launch_bounds__(NT, 4) k_gather_w(GatherArgs a) {
     const int64_t slot = (int64_t)(u - a.slot_lo);
     if (a.summ && whole) {
       // first fit, one piece: the summary straight from the bitmap
-      const int32_t so = a.s_own[w];
-      warp_summarize(s_bm, a.words, so, a.T, (so > a.T) ? a.kofs[p0 + rel_hi] : 0, adjm,
-                     a.gsum + slot * kSumInts, a.lbm + slot * a.words);
+      int32_t *rec = a.gsum + slot * kSumInts;
+      int32_t got = 0, q0 = 0;
+      warp_first_free_from<kSumCand>(s_bm, W4, qor, rec, got, q0);
+      if (got < kSumCand) {  // past the groups ORed so far: the rest of the hubs
+        if (hubs && qor < W4) {
+          warp_hub_or(s_bm4, nb4, W4, hubs, hub, qor, W4);
+          n_hub_groups += (unsigned long long)__popc(hubs) * (W4 - qor);
+        }
+        warp_first_free_from<kSumCand>(s_bm, W4, INT32_MAX, rec, got, q0);
+      }
+      warp_summarize_rest(s_bm, so, a.T, (so > a.T) ? a.kofs[p0 + rel_hi] : 0, adjm, rec,
+                          a.lbm + slot * a.words);
       warp_clear(s_bm4, W4);
       continue;
     }
@@ -1292,6 +1337,11 @@ __global__ void __launch_bounds__(NT, 4) k_gather_w(GatherArgs a) {
       }
     }
     __syncwarp();
+  }
+  if (lane == 0 && n_hub_pairs) {
+    atomicAdd(&a.dev->trav_hub, n_trav_hub);
+    atomicAdd(&a.dev->hub_pairs, n_hub_pairs);
+    atomicAdd(&a.dev->hub_words, 4 * n_hub_groups);
   }
 }
 

@@ -65,10 +65,11 @@ struct DevScalars {
   unsigned long long trav_large, incid_large, w_large;  // the same over gathered (large) vertices
   unsigned long long trav_hub;   // two-hop entries of hub nets, read as bitmaps instead
   unsigned long long hub_pairs;  // (vertex, hub net) pairs gathered from bitmaps
+  unsigned long long hub_words;  // hub bitmap words ORed by those pairs
   unsigned long long acc[4]; // reductions (statistics)
   unsigned long long incid_next;  // sum over W_{r+1} of |nets(w)| (set by the compaction)
 };
-constexpr int kRoundCounters = 7;  // trav .. hub_pairs, zeroed at the start of a round
+constexpr int kRoundCounters = 8;  // trav .. hub_words, zeroed at the start of a round
 constexpr int32_t kHubMin = 1024;  // a hub net has more members than this and than the
                                    // round's bitmap words
 
@@ -161,8 +162,8 @@ int launch_vertex_static(const bgpc_graph_t &g, const int32_t *tpos, int32_t *s_
 int launch_net_static(const bgpc_graph_t &g, int32_t T, int32_t *bigt, int32_t *bigd,
                        DevScalars *dev, cudaStream_t s);
 int launch_init_queue(const int32_t *rank, int32_t n_a, int32_t *W, int32_t *err, cudaStream_t s);
-int launch_init_mirror(const bgpc_graph_t &g, const int32_t *rank, const int32_t *tpos,
-                        int32_t *nc, int32_t *npos, int32_t *colors, int sms, cudaStream_t s);
+int launch_init_mirror(const bgpc_graph_t &g, const int32_t *rank, int32_t *nc, int32_t *npos,
+                       int32_t *colors, int sms, cudaStream_t s);
 int launch_closed_nbhd(const bgpc_ugraph_t &g, int32_t *cptr, int32_t *cidx, int sms,
                         cudaStream_t s);
 
@@ -201,6 +202,7 @@ struct GatherArgs {
   uint32_t *gbm;
   unsigned long long *gadj;
   const int32_t *b_idx;        // vtxs lists (chunk-mate search in hub nets)
+  const int32_t *tpos;         // CSR entry (w, v) -> CSC index of w in vtxs(v)
   const int32_t *hub_id;       // net -> hub slot or -1
   const uint32_t *nbm;         // hub color bitmaps [nhub][words] (the wave snapshot)
   DevScalars *dev;             // hub counters

@@ -139,24 +139,23 @@ __global__ void k_queue_check(const int32_t *__restrict__ rank, int32_t n,
   if (w < 0 || w >= n || rank[w] != (int32_t)p) atomicOr(err, ERR_RANK);
 }
 
-// Round 1: every vertex is in W at position pos = rank[w] (or w).
-__global__ void k_init_mirror(const int32_t *__restrict__ a_ptr, const int32_t *__restrict__ rank,
-                              const int32_t *__restrict__ tpos, int32_t n_a,
+// The net-major mirrors at the start: every member is uncolored and in W_0
+// at position pos(u) = rank[u] (or u), so nc[f] = -2 - pos and npos[f] = pos
+// for the CSC entry f of member u.  Written in CSC order (coalesced; only
+// rank is read at random), and c <- -1.
+__global__ void k_init_mirror(const int32_t *__restrict__ b_idx, int64_t nnz,
+                              const int32_t *__restrict__ rank, int32_t n_a,
                               int32_t *__restrict__ nc, int32_t *__restrict__ npos,
                               int32_t *__restrict__ colors) {
-  const int lane = threadIdx.x & 31;
-  int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t w = warp; w < n_a; w += nwarps) {
-    int32_t pos = rank ? rank[w] : (int32_t)w;
-    int32_t beg = a_ptr[w], end = a_ptr[w + 1];
-    for (int32_t i = beg + lane; i < end; i += 32) {
-      int32_t f = tpos[i];
-      nc[f] = -2 - pos;
-      npos[f] = pos;
-    }
-    if (lane == 0) colors[w] = -1;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; f < nnz; f += stride) {
+    const int32_t u = b_idx[f];
+    const int32_t pos = rank ? rank[u] : u;
+    nc[f] = -2 - pos;
+    npos[f] = pos;
   }
+  for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < n_a; w += stride)
+    colors[w] = -1;
 }
 
 // N[u] = adj(u) with u inserted at its sorted place: cptr[u] = ptr[u] + u.
@@ -240,11 +239,13 @@ int launch_init_queue(const int32_t *rank, int32_t n_a, int32_t *W, int32_t *err
   return rank ? 2 : 1;
 }
 
-int launch_init_mirror(const bgpc_graph_t &g, const int32_t *rank, const int32_t *tpos,
-                        int32_t *nc, int32_t *npos, int32_t *colors, int sms, cudaStream_t s) {
+int launch_init_mirror(const bgpc_graph_t &g, const int32_t *rank, int32_t *nc, int32_t *npos,
+                        int32_t *colors, int sms, cudaStream_t s) {
   if (g.n_a <= 0) return 0;
-  k_init_mirror<<<grid_warps(g.n_a, sms), kNT, 0, s>>>(g.a_ptr, rank, tpos, g.n_a, nc, npos,
-                                                        colors);
+  const int64_t n = (int64_t)g.nnz > (int64_t)g.n_a ? (int64_t)g.nnz : (int64_t)g.n_a;
+  const int64_t cap = (int64_t)sms * 8;
+  const int64_t grid = div_up(n, (int64_t)kNT) < cap ? div_up(n, (int64_t)kNT) : cap;
+  k_init_mirror<<<(int)grid, kNT, 0, s>>>(g.b_idx, g.nnz, rank, g.n_a, nc, npos, colors);
   return 1;
 }
 
