@@ -828,34 +828,42 @@ __device__ __forceinline__ void take(int32_t x, uint32_t *s_bm, int32_t lim, int
 }
 
 // The lanes of a warp stream src[0, n) (scalar head to a 16-byte boundary,
-// int4 body with four loads in flight per lane, scalar tail).
+// int4 body, scalar tail); the head, the tail and the first four int4 groups
+// of every lane are loaded together, so a net of up to ~512 members costs one
+// round trip.
 __device__ __forceinline__ void warp_stream(const int32_t *__restrict__ src, int32_t n,
                                             uint32_t *s_bm, int32_t lim, int32_t p0,
                                             int32_t rel_hi, unsigned long long &adj) {
   const int lane = threadIdx.x & 31;
   const int32_t mis = (int32_t)((reinterpret_cast<uintptr_t>(src) >> 2) & 3);
   const int32_t head = mis ? min(n, 4 - mis) : 0;
-  if (lane < head) take(__ldg(src + lane), s_bm, lim, p0, rel_hi, adj);
   const int4 *v = reinterpret_cast<const int4 *>(src + head);
   const int32_t nv = (n - head) >> 2;
-  for (int32_t i0 = lane; i0 < nv; i0 += 128) {
+  const int32_t t0 = head + (nv << 2);
+  const bool hv = lane < head, tv = t0 + lane < n;
+  const int32_t hx = hv ? __ldg(src + lane) : 0;
+  const int32_t tx = tv ? __ldg(src + t0 + lane) : 0;
+  for (int32_t b0 = 0;; b0 += 128) {
     int4 q[4];
 #pragma unroll
     for (int k = 0; k < 4; k++) {
-      const int32_t i = i0 + 32 * k;
-      q[k] = (i < nv) ? __ldg(v + i) : make_int4(INT32_MIN, INT32_MIN, INT32_MIN, INT32_MIN);
+      const int32_t i = b0 + lane + 32 * k;
+      q[k] = (i < nv) ? __ldg(v + i) : make_int4(0, 0, 0, 0);
+    }
+    if (b0 == 0) {
+      if (hv) take(hx, s_bm, lim, p0, rel_hi, adj);
+      if (tv) take(tx, s_bm, lim, p0, rel_hi, adj);
     }
 #pragma unroll
     for (int k = 0; k < 4; k++) {
-      if (q[k].x == INT32_MIN) continue;
+      if (b0 + lane + 32 * k >= nv) continue;
       take(q[k].x, s_bm, lim, p0, rel_hi, adj);
       take(q[k].y, s_bm, lim, p0, rel_hi, adj);
       take(q[k].z, s_bm, lim, p0, rel_hi, adj);
       take(q[k].w, s_bm, lim, p0, rel_hi, adj);
     }
+    if (b0 + 128 >= nv) break;
   }
-  const int32_t t0 = head + (nv << 2);
-  if (t0 + lane < n) take(__ldg(src + t0 + lane), s_bm, lim, p0, rel_hi, adj);
 }
 
 // First index of the sorted list l[0, n) whose value is >= u.
