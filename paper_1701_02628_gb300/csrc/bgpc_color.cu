@@ -1215,23 +1215,46 @@ __global__ void __launch_bounds__(NT, 4) k_gather_w(GatherArgs a) {
       // before w's own entry (its CSC index tp): read backwards from there
       // while the ids stay >= id_lo (one window of 32 per step, usually one
       // step); the mirror words of those entries carry the queue positions.
-      for (unsigned hm = hubs; hm && rel_hi > 0; hm &= hm - 1u) {
+      // Four hubs per step: their first windows (ids and mirror words) are
+      // loaded together.
+      for (unsigned hm = hubs; hm && rel_hi > 0 && a.id_order;) {
+        int32_t f[4], hb[4], id[4], x[4];
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+          const bool val = hm != 0;
+          const int t = val ? __ffs(hm) - 1 : 0;
+          f[k] = __shfl_sync(kFull, tp, t) - 1 - lane;
+          hb[k] = val ? __shfl_sync(kFull, bp, t) : INT32_MAX;
+          hm &= hm - 1u;
+        }
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+          const bool ok = f[k] >= hb[k];
+          id[k] = ok ? __ldg(a.b_idx + f[k]) : INT32_MIN;
+          x[k] = ok ? a.nc[f[k]] : 0;
+        }
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+          bool in = id[k] >= id_lo;
+          int32_t xk = x[k];
+          // more than 32 entries with ids in [id_lo, w): the next windows
+          for (int32_t top = f[k] + lane - 32;;) {
+            const int32_t rel = (-2 - xk) - p0;
+            if (in && xk < 0 && rel >= 0 && rel < rel_hi) adj |= 1ull << rel;
+            if (__ballot_sync(kFull, in) != kFull) break;
+            const int32_t g = top - lane;
+            in = g >= hb[k] && __ldg(a.b_idx + g) >= id_lo;
+            xk = in ? a.nc[g] : 0;
+            top -= 32;
+          }
+        }
+      }
+      for (unsigned hm = hubs; hm && rel_hi > 0 && !a.id_order; hm &= hm - 1u) {
         const int t = __ffs(hm) - 1;
         const int32_t hbp = __shfl_sync(kFull, bp, t), hsz = __shfl_sync(kFull, sz, t);
-        if (a.id_order) {
-          for (int32_t top = __shfl_sync(kFull, tp, t) - 1;; top -= 32) {
-            const int32_t f = top - lane;
-            const bool in = f >= hbp && __ldg(a.b_idx + f) >= id_lo;
-            const int32_t x = in ? a.nc[f] : 0;
-            const int32_t rel = (-2 - x) - p0;
-            if (in && x < 0 && rel >= 0 && rel < rel_hi) adj |= 1ull << rel;
-            if (__ballot_sync(kFull, in) != kFull) break;
-          }
-        } else {
-          const int32_t *l = a.b_idx + hbp;
-          for (int32_t jj = lane; jj < rel_hi; jj += 32)
-            if (sorted_has(l, hsz, a.W[p0 + jj])) adj |= 1ull << jj;
-        }
+        const int32_t *l = a.b_idx + hbp;
+        for (int32_t jj = lane; jj < rel_hi; jj += 32)
+          if (sorted_has(l, hsz, a.W[p0 + jj])) adj |= 1ull << jj;
       }
       __syncwarp();
     }
