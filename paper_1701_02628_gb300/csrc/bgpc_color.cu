@@ -604,10 +604,34 @@ __global__ void __launch_bounds__(NT) k_color_wave(WaveArgs a) {
       __syncthreads();
     }
 
+    // ---- step P (first fit): a vertex with no earlier neighbour in its
+    // chunk sees no overlay, so its color follows from its own forbidden set
+    // alone; those vertices are colored all at once, one warp each
+    if constexpr (POLICY == BGPC_FF) {
+      for (int32_t iv = warp; iv < n; iv += NW) {
+        if (s_adj[iv] != 0ull) continue;
+        int32_t x;
+        const int32_t so = s_sown[iv];
+        if ((large >> iv) & 1ull) {
+          x = (so > a.T && s_rcnt[iv] > 0) ? s_rcand[iv][0] : s_cand[iv][0];
+        } else {
+          const uint32_t word = (lane < kWords) ? s_bm[iv][lane] : kFull;
+          x = (so > a.T) ? win_kth_free_down(word, so - 1, s_k[iv]) : -1;
+          if (x < 0) x = win_first_free_up(word, 0);
+          if (x < 0) {  // cannot happen within the window bounds
+            if (lane == 0) atomicOr(a.err, ERR_INTERNAL);
+            x = 0;
+          }
+        }
+        if (lane == 0) s_col[iv] = x;
+      }
+      __syncthreads();
+    }
+
     // ---- phase B: resolve the chunk's vertices in order.  One warp walks the
-    // chunk; it stops only at a vertex that needs the whole CTA (a large
-    // vertex under B1/B2, or a first-fit vertex whose overlay used up its
-    // candidates).
+    // chunk (under first fit only the vertices with earlier neighbours are
+    // left); it stops only at a vertex that needs the whole CTA (a large
+    // vertex under B1/B2).
     int32_t i = 0;
     while (i < n) {
       if (warp == 0) {
@@ -618,7 +642,9 @@ __global__ void __launch_bounds__(NT) k_color_wave(WaveArgs a) {
           if (lg && POLICY != BGPC_FF) break;
           const unsigned long long am = s_adj[ii];
           int32_t x = -1;
-          if (!lg) {
+          if (POLICY == BGPC_FF && am == 0ull) {
+            x = s_col[ii];  // step P
+          } else if (!lg) {
 #pragma unroll
             for (int h = 0; h < 2; h++) {
               const int32_t jj = lane + 32 * h;
