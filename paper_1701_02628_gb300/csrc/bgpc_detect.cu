@@ -59,6 +59,8 @@ __global__ void __launch_bounds__(kNT) k_kofs(const int32_t *__restrict__ b_ptr,
         pos = npos[f];
         flag = (pos >= 0 && nown[f]) ? 1 : 0;
       }
+      // after the first round most tiles hold no owner in W: one barrier
+      if (__syncthreads_count(flag) == 0) continue;
       int32_t total;
       int32_t ex = block_excl_scan<kNT>(flag, red, &total);
       if (flag) kofs[pos] = carry + ex;
