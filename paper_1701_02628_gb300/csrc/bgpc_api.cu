@@ -391,8 +391,13 @@ int color_impl(bgpc_ctx_t *ctx, const bgpc_graph_t &g, const bgpc_opts_t &o, int
     }
     nk += launch_compact(ctx->lose.p, W, m, ctx->newpos.p, Wn, ctx->blocksum.p, g.a_ptr,
                          ctx->dev, s);
-    nk += launch_relabel(g.a_ptr, ctx->tpos.p, W, m, ctx->lose.p, ctx->newpos.p, ctx->nc.p,
-                         ctx->npos.p, colors, sms, s);
+    // W large against the graph (the first round): relabel in CSC order
+    if (incid_w < 0 || incid_w * 4 > (int64_t)nnz)
+      nk += launch_relabel_csc(nnz, W, m, ctx->lose.p, ctx->newpos.p, ctx->nc.p, ctx->npos.p,
+                               colors, sms, s);
+    else
+      nk += launch_relabel(g.a_ptr, ctx->tpos.p, W, m, ctx->lose.p, ctx->newpos.p, ctx->nc.p,
+                           ctx->npos.p, colors, sms, s);
     nk += launch_gmax(colors, n_a, ctx->dev, s);
     tm.end(ev, PH_DETECT);
     CU(cudaGetLastError());

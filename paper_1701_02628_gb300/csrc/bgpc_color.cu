@@ -845,12 +845,10 @@ __global__ void __launch_bounds__(NT) k_color_wave(WaveArgs a) {
 // chunk-mate (queue position in [p0, p0 + rel_hi)) joins the adjacency mask.
 __device__ __forceinline__ void take(int32_t x, uint32_t *s_bm, int32_t lim, int32_t p0,
                                      int32_t rel_hi, unsigned long long &adj) {
-  if (x >= 0) {
-    if (x < lim) atomicOr(&s_bm[x >> 5], 1u << (x & 31));
-  } else {
-    const int32_t rel = (-2 - x) - p0;
-    if (rel >= 0 && rel < rel_hi) adj |= 1ull << rel;
-  }
+  // both tests without a branch between them (unsigned compares)
+  const uint32_t rel = 0xfffffffeu - (uint32_t)x - (uint32_t)p0;  // -2 - x - p0
+  if ((uint32_t)x < (uint32_t)lim) atomicOr(&s_bm[x >> 5], 1u << (x & 31));
+  if (x < 0 && rel < (uint32_t)rel_hi) adj |= 1ull << rel;
 }
 
 // The lanes of a warp stream src[0, n) (scalar head to a 16-byte boundary,

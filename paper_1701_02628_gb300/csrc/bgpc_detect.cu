@@ -355,6 +355,38 @@ __global__ void k_relabel(const int32_t *__restrict__ a_ptr, const int32_t *__re
   }
 }
 
+// The same relabelling in CSC order, for rounds whose W covers much of the
+// graph: every mirror entry of a W member (npos >= 0) is rewritten in place
+// (coalesced; lose and newpos are read at random but are n_a-sized), then
+// k_relabel_tail resets the losers' colors and all lose flags.
+__global__ void k_relabel_csc(int64_t nnz, uint8_t const *__restrict__ lose,
+                              const int32_t *__restrict__ newpos, int32_t *__restrict__ nc,
+                              int32_t *__restrict__ npos) {
+  for (int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; f < nnz;
+       f += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t p = npos[f];
+    if (p < 0) continue;
+    if (lose[p]) {
+      const int32_t np = newpos[p];
+      npos[f] = np;
+      nc[f] = -2 - np;
+    } else {
+      npos[f] = -1;
+    }
+  }
+}
+
+__global__ void k_relabel_tail(const int32_t *__restrict__ W, int32_t m,
+                               uint8_t *__restrict__ lose, int32_t *__restrict__ colors) {
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < m;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    if (lose[p]) {
+      colors[W[p]] = -1;
+      lose[p] = 0;
+    }
+  }
+}
+
 __global__ void k_gmax(const int32_t *__restrict__ colors, int32_t n, DevScalars *dev) {
   int32_t mx = -1;
   for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n;
@@ -440,6 +472,21 @@ int launch_compact(const uint8_t *lose, const int32_t *W, int32_t m, int32_t *ne
   k_scan_blocks<<<1, kScanNT, 0, s>>>(blocksum, nblocks, dev);
   k_scan_scatter<<<nblocks, kScanNT, 0, s>>>(lose, W, m, blocksum, newpos, Wn, a_ptr, dev);
   return 3;
+}
+
+int launch_relabel_csc(int64_t nnz, const int32_t *W, int32_t m, uint8_t *lose,
+                       const int32_t *newpos, int32_t *nc, int32_t *npos, int32_t *colors,
+                       int sms, cudaStream_t s) {
+  if (m <= 0) return 0;
+  const long long cap = (long long)sms * 8;
+  long long g1 = div_up(nnz, kNT);
+  if (g1 > cap) g1 = cap;
+  if (g1 < 1) g1 = 1;
+  k_relabel_csc<<<(int)g1, kNT, 0, s>>>(nnz, lose, newpos, nc, npos);
+  long long g2 = div_up(m, kNT);
+  if (g2 > cap) g2 = cap;
+  k_relabel_tail<<<(int)g2, kNT, 0, s>>>(W, m, lose, colors);
+  return 2;
 }
 
 int launch_relabel(const int32_t *a_ptr, const int32_t *tpos, const int32_t *W, int32_t m,

@@ -260,6 +260,9 @@ int launch_detect_pairs(const int32_t *a_ptr, const int32_t *a_idx, const int32_
 int launch_compact(const uint8_t *lose, const int32_t *W, int32_t m, int32_t *newpos,
                     int32_t *Wn, int32_t *blocksum, const int32_t *a_ptr, DevScalars *dev,
                     cudaStream_t s);
+int launch_relabel_csc(int64_t nnz, const int32_t *W, int32_t m, uint8_t *lose,
+                       const int32_t *newpos, int32_t *nc, int32_t *npos, int32_t *colors,
+                       int sms, cudaStream_t s);
 int launch_relabel(const int32_t *a_ptr, const int32_t *tpos, const int32_t *W, int32_t m,
                     uint8_t *lose, const int32_t *newpos, int32_t *nc, int32_t *npos,
                     int32_t *colors, int sms, cudaStream_t s);

@@ -52,6 +52,36 @@ __global__ void k_tpos(const int32_t *__restrict__ a_ptr, const int32_t *__restr
     for (int32_t i = beg + lane; i < end; i += 32) {
       int32_t v = a_idx[i];
       int32_t lo = b_ptr[v], hi = b_ptr[v + 1];
+      // first index of vtxs(v) holding an id >= w: a few interpolation
+      // steps on the ids at the ends of the range (the members of a net are
+      // spread over the id space, so each step shrinks the range to about
+      // its square root), then bisection of what is left
+      if (hi - lo > 16) {
+        int32_t a0 = lo, a1 = hi - 1;  // the answer lies in [a0, a1 + 1]
+        int32_t v0 = b_idx[a0], v1 = b_idx[a1];
+        for (int it = 0; it < 6 && a1 - a0 > 16 && v0 < (int32_t)w && (int32_t)w <= v1; it++) {
+          int32_t g = a0 + (int32_t)((int64_t)(a1 - a0) * ((int64_t)w - v0) / ((int64_t)v1 - v0));
+          g = min(max(g, a0 + 1), a1 - 1);
+          const int32_t vg = b_idx[g];
+          if (vg < (int32_t)w) {
+            a0 = g;
+            v0 = vg;
+          } else {
+            a1 = g;
+            v1 = vg;
+          }
+        }
+        if ((int32_t)w <= v0) {
+          lo = a0;
+          hi = a0;
+        } else if ((int32_t)w > v1) {
+          lo = a1 + 1;
+          hi = a1 + 1;
+        } else {
+          lo = a0 + 1;  // b_idx[a0] < w <= b_idx[a1]
+          hi = a1;
+        }
+      }
       while (lo < hi) {
         int32_t mid = lo + ((hi - lo) >> 1);
         if (b_idx[mid] < (int32_t)w) lo = mid + 1; else hi = mid;
