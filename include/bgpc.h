@@ -107,10 +107,16 @@ typedef struct {
                                 scanned) or BGPC_DETECT_PAIRS (only the (W member,
                                 net) pairs, through a hash table); a mapping
                                 parameter, results do not change */
-    int32_t reserved[3];
+    int32_t gather;          /* large-vertex gather: BGPC_GATHER_AUTO (0: one warp per
+                                piece with its own bitmap when eight bitmaps fit in
+                                a CTA's shared memory, else one CTA per piece) or
+                                BGPC_GATHER_CTA (1: always one CTA per piece); a
+                                mapping parameter, results do not change */
+    int32_t reserved[2];
 } bgpc_opts_t;
 
 enum { BGPC_DETECT_AUTO = 0, BGPC_DETECT_NETS = 1, BGPC_DETECT_PAIRS = 2 };
+enum { BGPC_GATHER_AUTO = 0, BGPC_GATHER_CTA = 1 };
 
 /* Statistics of one call (host struct). */
 typedef struct {

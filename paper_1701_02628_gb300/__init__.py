@@ -24,6 +24,7 @@ BGPC_EINVAL, BGPC_ENOMEM, BGPC_ECUDA, BGPC_EROUNDS = -1, -2, -3, -4
 BGPC_ETIMEOUT, BGPC_EUNSORTED, BGPC_EINTERNAL = -5, -6, -7
 BGPC_FF, BGPC_B1, BGPC_B2, BGPC_B2X = 0, 1, 2, 3
 BGPC_DETECT_AUTO, BGPC_DETECT_NETS, BGPC_DETECT_PAIRS = 0, 1, 2
+BGPC_GATHER_AUTO, BGPC_GATHER_CTA = 0, 1
 BGPC_MAX_REPORT = 64
 NO_BIG = (1 << 31) - 1
 
@@ -49,7 +50,7 @@ class bgpc_opts_t(ctypes.Structure):
                 ("W_out", ctypes.c_void_p), ("want_balance", ctypes.c_int32),
                 ("profile", ctypes.c_int32), ("stop_before_removal", ctypes.c_int32),
                 ("batch_streams", ctypes.c_int32), ("detect", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 3)]
+                ("gather", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
 
 
 class bgpc_stats_t(ctypes.Structure):
@@ -251,7 +252,7 @@ def bgpc_opts_default() -> bgpc_opts_t:
 def make_opts(policy=BGPC_FF, chunk=64, waves=16, big_net=64, rank=None, max_rounds=1000,
               validate=False, stop_after_waves=0, W_out=None, want_balance=False,
               profile=False, stop_before_removal=False, batch_streams=0,
-              detect=BGPC_DETECT_AUTO) -> bgpc_opts_t:
+              detect=BGPC_DETECT_AUTO, gather=BGPC_GATHER_AUTO) -> bgpc_opts_t:
     o = bgpc_opts_default()
     o.policy, o.chunk, o.waves, o.big_net = policy, chunk, waves, big_net
     o.rank = _ptr(rank)
@@ -264,6 +265,7 @@ def make_opts(policy=BGPC_FF, chunk=64, waves=16, big_net=64, rank=None, max_rou
     o.stop_before_removal = int(bool(stop_before_removal))
     o.batch_streams = batch_streams
     o.detect = detect
+    o.gather = gather
     return o
 
 

@@ -61,6 +61,7 @@ int check_opts(const bgpc_opts_t *o) {
   if (!o) return BGPC_EINVAL;
   if (o->policy < BGPC_FF || o->policy > BGPC_B2X) return BGPC_EINVAL;
   if (o->detect < BGPC_DETECT_AUTO || o->detect > BGPC_DETECT_PAIRS) return BGPC_EINVAL;
+  if (o->gather < BGPC_GATHER_AUTO || o->gather > BGPC_GATHER_CTA) return BGPC_EINVAL;
   if (o->chunk < 1 || o->chunk > kMaxChunk) return BGPC_EINVAL;
   if (o->waves < 1 || o->big_net < 0 || o->max_rounds < 1 || o->stop_after_waves < 0)
     return BGPC_EINVAL;
@@ -320,7 +321,7 @@ int color_impl(bgpc_ctx_t *ctx, const bgpc_graph_t &g, const bgpc_opts_t &o, int
         ga.gsum = ctx->gsum.p;
         ga.lbm = ctx->lbm.p;
         ev = tm.begin();
-        CU(launch_gather(ga, sms, s));
+        CU(launch_gather(ga, o.gather == BGPC_GATHER_CTA, sms, s));
         tm.end(ev, PH_GATHER);
         nk++;
         WaveArgs a;

@@ -768,9 +768,14 @@ __global__ void __launch_bounds__(NT) k_color_wave(WaveArgs a) {
       }
       __syncthreads();
       const int32_t L = s_state[3];
-      if (L < n) {
+      if (POLICY == BGPC_FF && L < n) {  // the first-fit walk never stops early
+        if (tid == 0) atomicOr(a.err, ERR_INTERNAL);
+        break;
+      }
+      if (POLICY != BGPC_FF && L < n) {
         // ---- CTA-wide path: the vertex's gathered forbidden set (k_gather)
-        // in shared memory, searched with block-wide reductions
+        // in shared memory, searched with block-wide reductions (B1/B2 only:
+        // first fit launches without the dynamic shared bitmap)
         const int64_t slot = slot0 + L;
         uint4 *gsrc = reinterpret_cast<uint4 *>(a.gbm + slot * a.words);
         uint4 *sdst = reinterpret_cast<uint4 *>(s_big);
@@ -1546,7 +1551,8 @@ cudaError_t allow_dynamic_smem(K kern) {
 template <int POLICY>
 cudaError_t launch_policy(const WaveArgs &a, int sms, cudaStream_t s) {
   auto kern = k_color_wave<POLICY, kWaveNT>;
-  const size_t smem = (size_t)a.words * 4;
+  // first fit resolves from the gather's summaries: no bitmap in shared memory
+  const size_t smem = (POLICY == BGPC_FF) ? 0 : (size_t)a.words * 4;
   cudaError_t e = allow_dynamic_smem(kern);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
@@ -1582,9 +1588,9 @@ cudaError_t launch_color_wave(int policy, const WaveArgs &a, int sms, cudaStream
   }
 }
 
-cudaError_t launch_gather(const GatherArgs &a, int sms, cudaStream_t s) {
+cudaError_t launch_gather(const GatherArgs &a, bool cta_only, int sms, cudaStream_t s) {
   if (a.slot_hi <= a.slot_lo) return cudaSuccess;
-  {  // warp-private pieces when eight bitmaps fit beside each other
+  if (!cta_only) {  // warp-private pieces when eight bitmaps fit beside each other
     auto kw = k_gather_w<kGatherNT>;
     const size_t smem_w = (size_t)(kGatherNT / 32) * a.words * 4;
     int dev = 0, optin = 0;

@@ -220,7 +220,7 @@ struct GatherArgs {
 // Largest bitmap (in words) the wave kernels can hold in shared memory.
 int32_t wave_max_words(int smem_optin);
 cudaError_t launch_color_wave(int policy, const WaveArgs &a, int sms, cudaStream_t s);
-cudaError_t launch_gather(const GatherArgs &a, int sms, cudaStream_t s);
+cudaError_t launch_gather(const GatherArgs &a, bool cta_only, int sms, cudaStream_t s);
 // Per round: pieces per wave-order slot, their prefix and the piece map.
 int launch_pieces(const int32_t *a_ptr, const int32_t *d2tot, const int32_t *W,
                   const int32_t *wlist, int32_t nch, int32_t C, int32_t m, int32_t small_ok,

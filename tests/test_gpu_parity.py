@@ -123,6 +123,21 @@ def test_detect_tiers(bg, ctx, policy, detect):
     assert st["rounds"] == 40
 
 
+@pytest.mark.parametrize("policy", [O.FF, O.B2])
+def test_gather_cta_form(bg, ctx, policy):
+    """The CTA-per-piece gather (taken by itself only for color bounds above
+    ~110k colors, where eight warp bitmaps no longer fit in shared memory),
+    forced on small graphs: hub nets, multi-piece vertices, rank order."""
+    g = hub_graph()
+    assert_parity(bg, ctx, g, policy=policy, gather=1)
+    rank = np.random.default_rng(9).permutation(g.n_a).astype(np.int32)
+    assert_parity(bg, ctx, g, policy=policy, rank=rank, gather=1)
+    g = gg.chung_lu(20000, 16, 1500, 2.1, seed=4)
+    assert_parity(bg, ctx, g, policy=policy, gather=1)
+    g = gg.from_nets(3000, [list(range(3000))])
+    assert_parity(bg, ctx, g, policy=policy, gather=1)
+
+
 @pytest.mark.parametrize("chunk,waves,big_net", [(1, 1, O.NO_BIG), (7, 3, 2), (32, 16, 0),
                                                  (64, 1, 8), (64, 64, O.NO_BIG), (13, 5, 64)])
 def test_semantic_parameters(bg, ctx, chunk, waves, big_net):
@@ -229,6 +244,10 @@ def test_errors(bg, ctx):
     for d in (-1, 3):
         with pytest.raises(bg.BgpcError) as e:
             bg.bgpc_color(ctx, dg, detect=d)
+        assert e.value.status == bg.BGPC_EINVAL
+    for v in (-1, 2):
+        with pytest.raises(bg.BgpcError) as e:
+            bg.bgpc_color(ctx, dg, gather=v)
         assert e.value.status == bg.BGPC_EINVAL
     bad_rank = torch.zeros(g.n_a, dtype=torch.int32, device="cuda:0")
     with pytest.raises(bg.BgpcError) as e:
