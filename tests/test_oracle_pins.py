@@ -314,3 +314,99 @@ def test_wave_stepping_reproduces_full_run():
     r2 = O.rs_color(g, pol, chunk=C, waves=Q, big_net=T, stop_after_waves=Q)
     if r2.status == O.STOPPED:
         assert np.array_equal(r2.W, st.W[lose.astype(bool)])
+
+
+# ------------------------------------------- validity counts and nbor sizes
+#
+# orc_conflicts, orc_d2_conflicts and orc_max_nbor underlie every validity
+# check and the greedy bound above, so they are pinned on hand-counted cases
+# and against the conflict graph written as an incidence-matrix product
+# (u ~ w iff row u and row w of the n_a x n_b incidence matrix B share a
+# column, i.e. (B B^T)[u, w] > 0 for u != w: Sec. II's definition of BGPC).
+
+def conflict_matrix(g):
+    B = np.zeros((g.n_a, g.n_b), np.int64)
+    rows = np.repeat(np.arange(g.n_a), np.diff(g.a_ptr))
+    B[rows, g.a_idx] = 1
+    M = (B @ B.T) > 0
+    np.fill_diagonal(M, False)
+    return M
+
+
+def test_conflicts_hand_counts():
+    """Counts of vertices that are uncolored or clash, derived by hand."""
+    g = gg.from_nets(4, [[0, 1, 2, 3]])
+    assert O.conflicts(g, [0, 0, 1, 1]) == 4     # two clashing pairs
+    assert O.conflicts(g, [0, 1, 2, 2]) == 2     # one clashing pair
+    assert O.conflicts(g, [0, 1, 2, 3]) == 0
+    assert O.conflicts(g, [-1, 1, 2, 3]) == 1    # uncolored counts
+    assert O.conflicts(g, [-1, -1, 2, 3]) == 2   # two uncolored (-1 == -1 is no clash
+                                                 # on top: each is counted once)
+    path = gg.from_nets(3, [[0, 1], [1, 2]])
+    assert O.conflicts(path, [0, 0, 0]) == 3
+    assert O.conflicts(path, [0, 1, 0]) == 0     # 0 and 2 share no net
+    assert O.conflicts(path, [0, 0, 1]) == 2
+    # a vertex clashing in two nets is counted once
+    two = gg.from_nets(3, [[0, 1], [0, 2]])
+    assert O.conflicts(two, [5, 5, 5]) == 3
+    # a vertex without nets never clashes
+    iso = gg.from_nets(3, [[0, 1]])
+    assert O.conflicts(iso, [7, 8, 7]) == 0
+
+
+def test_conflicts_against_incidence_matrix():
+    rng = np.random.default_rng(31)
+    for _ in range(60):
+        n_a, n_b = int(rng.integers(1, 14)), int(rng.integers(1, 9))
+        g, _ = random_tiny(rng, n_a, n_b, 5)
+        M = conflict_matrix(g)
+        c = rng.integers(-1, 4, size=n_a).astype(np.int32)
+        same = (c[:, None] == c[None, :]) & M
+        want = int(((c < 0) | same.any(axis=1)).sum())
+        assert O.conflicts(g, c) == want
+
+
+def test_max_nbor_hand_counts():
+    # two vertices sharing two nets are one neighbour of each other
+    g = gg.from_nets(2, [[0, 1], [0, 1]])
+    best, sizes = O.max_nbor(g)
+    assert best == 1 and sizes.tolist() == [1, 1]
+    # one net of size s: s - 1 neighbours each
+    for s in [1, 2, 9]:
+        best, sizes = O.max_nbor(gg.from_nets(s, [list(range(s))]))
+        assert best == s - 1 and sizes.tolist() == [s - 1] * s
+    # overlapping nets {0,1,2}, {2,3}: vertex 2 sees 0, 1, 3 once each
+    best, sizes = O.max_nbor(gg.from_nets(5, [[0, 1, 2], [2, 3]]))
+    assert best == 3 and sizes.tolist() == [2, 2, 3, 1, 0]
+
+
+@pytest.mark.parametrize("n", [5, 6, 9])
+def test_max_nbor_stencil_closed_form(n):
+    """9-point stencil: columns conflict iff |di| <= 2 and |dj| <= 2, so
+    |nbor(i, j)| = (min(i,2) + min(n-1-i,2) + 1) (same for j) - 1: 24 inside,
+    14 on an edge, 8 in a corner."""
+    g = gg.stencil9(n)
+    i, j = np.divmod(np.arange(n * n), n)
+    span = lambda x: np.minimum(x, 2) + np.minimum(n - 1 - x, 2) + 1
+    best, sizes = O.max_nbor(g)
+    assert np.array_equal(sizes, span(i) * span(j) - 1)
+    assert best == 24 and sizes[0] == 8 and sizes[2] == 14
+
+
+def test_max_nbor_against_incidence_matrix():
+    rng = np.random.default_rng(37)
+    for _ in range(40):
+        g, _ = random_tiny(rng, int(rng.integers(1, 16)), int(rng.integers(1, 10)), 6)
+        best, sizes = O.max_nbor(g)
+        want = conflict_matrix(g).sum(axis=1)
+        assert np.array_equal(sizes, want) and best == int(want.max(initial=0))
+
+
+def test_d2_conflicts_hand_counts():
+    """Direct distance-2 check on a path 0-1-2-3 (Sec. II)."""
+    ug = gg.from_edges(4, [(0, 1), (1, 2), (2, 3)])
+    assert O.d2_conflicts(ug, [0, 1, 2, 0]) == 0   # 0 and 3 are at distance 3
+    assert O.d2_conflicts(ug, [0, 1, 0, 2]) == 2   # 0 and 2 at distance 2
+    assert O.d2_conflicts(ug, [0, 0, 1, 2]) == 2   # adjacent clash
+    assert O.d2_conflicts(ug, [0, 1, -1, 0]) == 1  # uncolored
+    assert O.d2_conflicts(ug, [0, 0, 0, 0]) == 4
