@@ -40,7 +40,7 @@ extern "C" {
 #define BGPC_ENOMEM (-2)      /* device allocation failed */
 #define BGPC_ECUDA (-3)       /* a CUDA runtime call failed */
 #define BGPC_EROUNDS (-4)     /* more than opts.max_rounds rounds */
-#define BGPC_ETIMEOUT (-5)    /* a bounded device wait gave up */
+#define BGPC_ETIMEOUT (-5)    /* opts.timeout_us exceeded */
 #define BGPC_EUNSORTED (-6)   /* adjacency not sorted / not unique / CSR and CSC disagree */
 #define BGPC_EINTERNAL (-7)   /* a device-side consistency check failed */
 
@@ -112,7 +112,16 @@ typedef struct {
                                 a CTA's shared memory, else one CTA per piece) or
                                 BGPC_GATHER_CTA (1: always one CTA per piece); a
                                 mapping parameter, results do not change */
-    int32_t reserved[2];
+    int32_t net_rounds;      /* semantic: the first net_rounds rounds are colored net by
+                                net (Alg. 8; Alg. 9 for D2GC) instead of by vertex
+                                waves: 0 = V-* (default), 1 = N1-*, 2 = N2-* of Sec. VI;
+                                see bgpc_color */
+    int64_t timeout_us;      /* > 0: wall-clock limit of the call in microseconds,
+                                checked each time the host waits for the device (after
+                                the setup and after every round); when exceeded the
+                                call returns BGPC_ETIMEOUT (outputs undefined).
+                                0 = no limit */
+    int32_t reserved[4];
 } bgpc_opts_t;
 
 enum { BGPC_DETECT_AUTO = 0, BGPC_DETECT_NETS = 1, BGPC_DETECT_PAIRS = 2 };
@@ -143,6 +152,8 @@ typedef struct {
     int64_t hub_pairs;   /* all rounds: (vertex, hub net) pairs so read */
     int64_t hub_words;   /* all rounds: bitmap words so read (under first fit a one-piece
                             vertex reads only the words its summary needs) */
+    double ms_total;     /* host wall-clock time of the whole call (it synchronises its
+                            stream, so this covers all of its device work) */
 } bgpc_stats_t;
 
 /* Fill `opts` with the defaults: FF, C=64, Q=16, T=64, id order,
@@ -199,18 +210,22 @@ int bgpc_color_sets(bgpc_ctx_t *ctx, const int32_t *colors, int32_t n, int64_t *
 
 /* Color-set statistics that allocate nothing (no counterpart in the paper:
  * this is a calling convention, not a step of the method).  For callers that
- * cannot allocate device memory: code running during CUDA graph capture,
- * code under an allocator that owns the whole device memory budget, and
- * latency-critical loops that must not enter the allocator.  Same results as
+ * cannot allocate device memory: code under an allocator that owns the whole
+ * device memory budget (a framework's caching allocator, a fixed budget), and
+ * latency-critical loops that must not enter the driver's allocator, whose
+ * cudaMalloc / cudaFree can synchronise the device.  Same results as
  * bgpc_color_sets without the cardinality array and without a context: the
  * histogram lives in a fixed device array of BGPC_NOALLOC_MAX_COLORS 64-bit
  * counters (8 MiB, held by every GPU that loads the library until exit).
- * colors: device int32 [n], each in [0, max_colors); max_colors in
- * [1, BGPC_NOALLOC_MAX_COLORS], else BGPC_EINVAL (also for a color out of
- * range).  Outputs are host pointers (each may be NULL).  The first call on a
- * device looks up the array's device address (make it before any stream
- * capture).  All calls share the array: calls that overlap on the GPU race.
- * Synchronises `stream`. */
+ * colors: device int32 [n] on the current device, each in [0, max_colors);
+ * max_colors in [1, BGPC_NOALLOC_MAX_COLORS], else BGPC_EINVAL (also for a
+ * color out of range, and for a colors array on another device or in
+ * unregistered host memory).  Outputs are host pointers (each may be NULL).
+ * The first call on a device looks up the array's device address (make it
+ * before any stream capture; after cudaDeviceReset the cached address is
+ * stale, so do not call it again in that process).  All calls share the
+ * array: calls that overlap on the GPU race.  Copies the accumulators to the
+ * host and synchronises `stream`. */
 #define BGPC_NOALLOC_MAX_COLORS (1 << 20)
 int bgpc_color_sets_noalloc(const int32_t *colors, int32_t n, int32_t max_colors,
                             int32_t *n_sets, int32_t *max_card, double *mean_card,

@@ -50,7 +50,8 @@ class bgpc_opts_t(ctypes.Structure):
                 ("W_out", ctypes.c_void_p), ("want_balance", ctypes.c_int32),
                 ("profile", ctypes.c_int32), ("stop_before_removal", ctypes.c_int32),
                 ("batch_streams", ctypes.c_int32), ("detect", ctypes.c_int32),
-                ("gather", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
+                ("gather", ctypes.c_int32), ("net_rounds", ctypes.c_int32),
+                ("timeout_us", ctypes.c_int64), ("reserved", ctypes.c_int32 * 4)]
 
 
 class bgpc_stats_t(ctypes.Structure):
@@ -68,7 +69,8 @@ class bgpc_stats_t(ctypes.Structure):
                 ("ms_setup", ctypes.c_double), ("ms_color", ctypes.c_double),
                 ("ms_publish", ctypes.c_double), ("ms_detect", ctypes.c_double),
                 ("ms_gather", ctypes.c_double), ("trav_hub", ctypes.c_int64),
-                ("hub_pairs", ctypes.c_int64), ("hub_words", ctypes.c_int64)]
+                ("hub_pairs", ctypes.c_int64), ("hub_words", ctypes.c_int64),
+                ("ms_total", ctypes.c_double)]
 
 
 EXPORTS = ["bgpc_opts_default", "bgpc_ctx_create", "bgpc_ctx_destroy", "bgpc_color",
@@ -173,6 +175,13 @@ def _ptr(t, dtype=torch.int32):
     return ctypes.c_void_p(t.data_ptr())
 
 
+def _check_n(t):
+    """Element counts travel as int32 through the C ABI: refuse larger ones
+    instead of letting ctypes wrap them."""
+    if t.numel() > (1 << 31) - 1:
+        raise ValueError(f"{t.numel()} elements exceed the C ABI's int32 sizes")
+
+
 def _fptr(t):
     return _ptr(t, torch.float32)
 
@@ -252,7 +261,8 @@ def bgpc_opts_default() -> bgpc_opts_t:
 def make_opts(policy=BGPC_FF, chunk=64, waves=16, big_net=64, rank=None, max_rounds=1000,
               validate=False, stop_after_waves=0, W_out=None, want_balance=False,
               profile=False, stop_before_removal=False, batch_streams=0,
-              detect=BGPC_DETECT_AUTO, gather=BGPC_GATHER_AUTO) -> bgpc_opts_t:
+              detect=BGPC_DETECT_AUTO, gather=BGPC_GATHER_AUTO, net_rounds=0,
+              timeout_us=0) -> bgpc_opts_t:
     o = bgpc_opts_default()
     o.policy, o.chunk, o.waves, o.big_net = policy, chunk, waves, big_net
     o.rank = _ptr(rank)
@@ -266,6 +276,8 @@ def make_opts(policy=BGPC_FF, chunk=64, waves=16, big_net=64, rank=None, max_rou
     o.batch_streams = batch_streams
     o.detect = detect
     o.gather = gather
+    o.net_rounds = net_rounds
+    o.timeout_us = timeout_us
     return o
 
 
@@ -281,7 +293,8 @@ def stats_dict(st: bgpc_stats_t) -> dict:
                 kernel_launches=st.kernel_launches,
                 color_launches=st.color_launches, ms_setup=st.ms_setup, ms_color=st.ms_color,
                 ms_publish=st.ms_publish, ms_detect=st.ms_detect, ms_gather=st.ms_gather,
-                trav_hub=st.trav_hub, hub_pairs=st.hub_pairs, hub_words=st.hub_words)
+                trav_hub=st.trav_hub, hub_pairs=st.hub_pairs, hub_words=st.hub_words,
+                ms_total=st.ms_total)
 
 
 def bgpc_color(ctx: Context, g: DeviceGraph, colors: torch.Tensor = None, stream=None, **opts):
@@ -341,6 +354,7 @@ def bgpc_validate(ctx: Context, g: DeviceGraph, colors: torch.Tensor, stream=Non
 
 def bgpc_color_sets(ctx: Context, colors: torch.Tensor, max_colors: int, stream=None):
     """Color-set cardinalities and statistics (bgpc_color_sets)."""
+    _check_n(colors)
     card = torch.zeros(max(max_colors, 1), dtype=torch.int64, device=colors.device)
     ns, mx = ctypes.c_int32(0), ctypes.c_int32(0)
     mean, std = ctypes.c_double(0), ctypes.c_double(0)
@@ -354,15 +368,21 @@ def bgpc_color_sets(ctx: Context, colors: torch.Tensor, max_colors: int, stream=
 
 def bgpc_color_sets_noalloc(colors: torch.Tensor, max_colors: int, stream=None) -> dict:
     """Color-set statistics without any device allocation
-    (bgpc_color_sets_noalloc): for callers that cannot allocate, e.g. during
-    CUDA graph capture or under a fixed memory budget.  Calls that overlap on
+    (bgpc_color_sets_noalloc): for callers that cannot allocate, e.g. under
+    an allocator that owns the whole memory budget or in loops that must not
+    enter the driver's allocator.  Runs on the device that holds ``colors``
+    (and, unless given, that device's current stream).  Calls that overlap on
     the GPU race (they share one fixed scratch array)."""
+    _check_n(colors)
     ns, mx = ctypes.c_int32(0), ctypes.c_int32(0)
     mean, std = ctypes.c_double(0), ctypes.c_double(0)
-    _check(load().bgpc_color_sets_noalloc(_ptr(colors), colors.numel(), max_colors,
-                                          ctypes.byref(ns), ctypes.byref(mx), ctypes.byref(mean),
-                                          ctypes.byref(std), _stream(stream)),
-           "bgpc_color_sets_noalloc")
+    with torch.cuda.device(colors.device):
+        st = _stream(stream) if stream is not None else \
+            ctypes.c_void_p(torch.cuda.current_stream(colors.device).cuda_stream)
+        _check(load().bgpc_color_sets_noalloc(_ptr(colors), colors.numel(), max_colors,
+                                              ctypes.byref(ns), ctypes.byref(mx),
+                                              ctypes.byref(mean), ctypes.byref(std), st),
+               "bgpc_color_sets_noalloc")
     return dict(n_sets=ns.value, max_card=mx.value, mean_card=mean.value, std_card=std.value)
 
 

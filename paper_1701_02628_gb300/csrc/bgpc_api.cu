@@ -5,6 +5,7 @@
 #include <string.h>
 
 #include <atomic>
+#include <chrono>
 #include <thread>
 #include <vector>
 
@@ -25,6 +26,19 @@ struct Guard {  // restores the caller's current device
     cudaGetDevice(&cur);
     if (prev >= 0 && cur != prev) cudaSetDevice(prev);
   }
+};
+
+// Wall-clock limit of one call (opts.timeout_us), checked where the host
+// waits for the device anyway; the round loop itself has no device-side wait.
+struct Deadline {
+  using clk = std::chrono::steady_clock;
+  clk::time_point t0 = clk::now();
+  int64_t limit_us;
+  explicit Deadline(int64_t us) : limit_us(us) {}
+  double ms() const {
+    return std::chrono::duration<double, std::milli>(clk::now() - t0).count();
+  }
+  bool passed() const { return limit_us > 0 && ms() * 1000.0 > (double)limit_us; }
 };
 
 int err_to_status(int32_t err) {
@@ -65,6 +79,7 @@ int check_opts(const bgpc_opts_t *o) {
   if (o->chunk < 1 || o->chunk > kMaxChunk) return BGPC_EINVAL;
   if (o->waves < 1 || o->big_net < 0 || o->max_rounds < 1 || o->stop_after_waves < 0)
     return BGPC_EINVAL;
+  if (o->net_rounds != 0 || o->timeout_us < 0) return BGPC_EINVAL;
   return BGPC_OK;
 }
 
@@ -140,7 +155,7 @@ int ensure_table(bgpc_ctx_t *ctx, size_t entries, cudaStream_t s, int64_t *nk) {
 }
 
 int color_impl(bgpc_ctx_t *ctx, const bgpc_graph_t &g, const bgpc_opts_t &o, int32_t *colors,
-               bgpc_stats_t *stats, cudaStream_t s) {
+               bgpc_stats_t *stats, cudaStream_t s, const Deadline &dl) {
   bgpc_stats_t st;
   memset(&st, 0, sizeof(st));
   const int32_t n_a = g.n_a, n_b = g.n_b, nnz = g.nnz;
@@ -193,6 +208,7 @@ int color_impl(bgpc_ctx_t *ctx, const bgpc_graph_t &g, const bgpc_opts_t &o, int
   if ((rc = sync_scalars(ctx, s))) return rc;
   tm.collect();
   if (ctx->host->err) return err_to_status(ctx->host->err);
+  if (dl.passed()) return BGPC_ETIMEOUT;
   const int32_t nbig_t = ctx->host->nbig_t, nbig_d = ctx->host->nbig_d;
   const int32_t nhub = ctx->host->nhub;
   const int32_t maxnet = ctx->host->maxnet;
@@ -408,6 +424,7 @@ int color_impl(bgpc_ctx_t *ctx, const bgpc_graph_t &g, const bgpc_opts_t &o, int
       ctx->gbm_zeroed = 0;  // a kernel may have stopped before clearing its slots
       return err_to_status(ctx->host->err);
     }
+    if (dl.passed()) return BGPC_ETIMEOUT;
     if (r < BGPC_MAX_REPORT) {
       st.w_per_round[r] = m;
       st.trav_per_round[r] = (int64_t)ctx->host->trav;
@@ -454,6 +471,7 @@ int color_impl(bgpc_ctx_t *ctx, const bgpc_graph_t &g, const bgpc_opts_t &o, int
   st.ms_publish = tm.ms[PH_PUBLISH];
   st.ms_detect = tm.ms[PH_DETECT];
   st.ms_gather = tm.ms[PH_GATHER];
+  st.ms_total = dl.ms();
   if (stats) *stats = st;
   return BGPC_OK;
 }
@@ -540,7 +558,8 @@ int bgpc_color(bgpc_ctx_t *ctx, const bgpc_graph_t *g, const bgpc_opts_t *opts, 
   if ((rc = check_opts(opts))) return rc;
   if (g->n_a > 0 && !colors) return BGPC_EINVAL;
   Guard guard(ctx->device);
-  return color_impl(ctx, *g, *opts, colors, stats, (cudaStream_t)stream);
+  Deadline dl(opts->timeout_us);
+  return color_impl(ctx, *g, *opts, colors, stats, (cudaStream_t)stream, dl);
 }
 
 int bgpc_color_batched(bgpc_ctx_t *ctx, int32_t n_graphs, const bgpc_graph_t *graphs,
@@ -557,6 +576,7 @@ int bgpc_color_batched(bgpc_ctx_t *ctx, int32_t n_graphs, const bgpc_graph_t *gr
     if (graphs[k].n_a > 0 && !colors[k]) return BGPC_EINVAL;
   }
   Guard guard(ctx->device);
+  Deadline dl(opts->timeout_us);
   cudaStream_t s = (cudaStream_t)stream;
   int K = opts->batch_streams > 0 ? opts->batch_streams : 8;
   if (K > n_graphs) K = n_graphs;
@@ -588,7 +608,7 @@ int bgpc_color_batched(bgpc_ctx_t *ctx, int32_t n_graphs, const bgpc_graph_t *gr
       if (k >= n_graphs) return;
       memset(&per[(size_t)k], 0, sizeof(bgpc_stats_t));
       const int r = color_impl(ctx->subs[(size_t)w], graphs[k], *opts, colors[k],
-                               &per[(size_t)k], ctx->sub_streams[(size_t)w]);
+                               &per[(size_t)k], ctx->sub_streams[(size_t)w], dl);
       if (r != BGPC_OK) {
         int zero = 0;
         err.compare_exchange_strong(zero, r);
@@ -637,6 +657,7 @@ int bgpc_color_batched(bgpc_ctx_t *ctx, int32_t n_graphs, const bgpc_graph_t *gr
     tot.ms_detect += st.ms_detect;
     tot.ms_gather += st.ms_gather;
   }
+  tot.ms_total = dl.ms();
   if (stats) *stats = tot;
   return BGPC_OK;
 }
@@ -650,6 +671,7 @@ int d2gc_color(bgpc_ctx_t *ctx, const bgpc_ugraph_t *g, const bgpc_opts_t *opts,
   int rc = check_opts(opts);
   if (rc) return rc;
   Guard guard(ctx->device);
+  Deadline dl(opts->timeout_us);
   cudaStream_t s = (cudaStream_t)stream;
   if (opts->validate && g->n > 0) {
     if ((rc = validate_csr(ctx, g->ptr, g->idx, g->n, g->nnz, g->n, s))) return rc;
@@ -668,7 +690,7 @@ int d2gc_color(bgpc_ctx_t *ctx, const bgpc_ugraph_t *g, const bgpc_opts_t *opts,
   bg.b_ptr = ctx->cptr.p;
   bg.b_idx = ctx->cidx.p;
   bgpc_opts_t o = *opts;
-  return color_impl(ctx, bg, o, colors, stats, s);
+  return color_impl(ctx, bg, o, colors, stats, s, dl);
 }
 
 int bgpc_validate(bgpc_ctx_t *ctx, const bgpc_graph_t *g, const int32_t *colors, int64_t *n_bad,

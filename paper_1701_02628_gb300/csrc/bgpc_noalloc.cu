@@ -2,23 +2,27 @@
 //
 // bgpc_color_sets needs a caller-provided cardinality array, and the coloring
 // path keeps its histogram in context scratch that is grown with cudaMalloc.
-// Some callers can do neither: code that runs while a CUDA graph is being
-// captured (cudaMalloc is not capturable), code running under an allocator
-// that owns all device memory (a framework's caching allocator or a fixed
-// memory budget), and latency-critical loops that must never enter the
-// driver's allocator.  bgpc_color_sets_noalloc serves them: its histogram and
-// accumulators live in one file-scope device array of fixed size, so the call
-// allocates nothing.
+// Some callers can do neither: code running under an allocator that owns all
+// device memory (a framework's caching allocator or a fixed memory budget
+// leaves nothing for a second allocator), and latency-critical loops that
+// must never enter the driver's allocator (cudaMalloc and cudaFree can
+// synchronise the whole device).  bgpc_color_sets_noalloc serves them: its
+// histogram and accumulators live in one file-scope device array of fixed
+// size, so the call allocates nothing.
 //
 // Costs and rules of that choice:
 //  * every GPU that loads this library holds the array (8 MiB + 128 B) until
 //    the process exits;
 //  * host code cannot use the array's name as a device address; its address
 //    is looked up once per device with cudaGetSymbolAddress, on the first call
-//    made on that device (make that first call before any stream capture);
+//    made on that device (make that first call before any stream capture, and
+//    do not call it again after cudaDeviceReset: the cached address would be
+//    stale);
 //  * every call shares the array: calls that overlap on the GPU (other
 //    streams, other host threads) race and give wrong statistics;
-//  * colors must lie in [0, max_colors) with max_colors <= 2^20.
+//  * colors must lie in [0, max_colors) with max_colors <= 2^20, and the
+//    colors array must be reachable from the current device;
+//  * the call copies the accumulators to the host and synchronises `stream`.
 #include <math.h>
 
 #include <mutex>
@@ -98,6 +102,18 @@ extern "C" int bgpc_color_sets_noalloc(const int32_t *colors, int32_t n, int32_t
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
     cudaGetLastError();
     return BGPC_ECUDA;
+  }
+  if (n > 0) {
+    // the kernels run on the current device: a colors array on another one
+    // would be dereferenced through the wrong address space
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, colors) != cudaSuccess) {
+      cudaGetLastError();
+      return BGPC_EINVAL;
+    }
+    if (at.type == cudaMemoryTypeUnregistered ||
+        (at.type == cudaMemoryTypeDevice && at.device != dev))
+      return BGPC_EINVAL;
   }
   unsigned long long *scr = nullptr;
   {

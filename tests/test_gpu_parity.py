@@ -281,6 +281,17 @@ def test_errors(bg, ctx):
     with pytest.raises(bg.BgpcError) as e:
         bg.bgpc_color(ctx, clique, chunk=1, waves=1, big_net=bg.NO_BIG, max_rounds=5)
     assert e.value.status == bg.BGPC_EROUNDS
+    # wall-clock limit: a clique under the Jacobi reading takes 40 rounds; a
+    # 1 us limit has passed by the first wait for the device (after the setup)
+    with pytest.raises(bg.BgpcError) as e:
+        bg.bgpc_color(ctx, clique, chunk=1, waves=1, big_net=bg.NO_BIG, timeout_us=1)
+    assert e.value.status == bg.BGPC_ETIMEOUT
+    with pytest.raises(bg.BgpcError) as e:
+        bg.bgpc_color(ctx, dg, timeout_us=-1)
+    assert e.value.status == bg.BGPC_EINVAL
+    _, st, rc = bg.bgpc_color(ctx, clique, chunk=1, waves=1, big_net=bg.NO_BIG,
+                              timeout_us=60_000_000)
+    assert rc == bg.BGPC_OK and st["rounds"] == 40 and st["ms_total"] > 0
     # the context stays usable after errors
     assert_parity(bg, ctx, g)
 

@@ -1,7 +1,8 @@
 """The allocation-free color-set statistics entry point.
 
-Some callers cannot allocate device memory (code running during CUDA graph
-capture, or under an allocator that owns the whole memory budget).
+Some callers cannot allocate device memory: code under an allocator that
+owns the whole memory budget, or loops that must not enter the driver's
+allocator (cudaMalloc and cudaFree can synchronise the device).
 bgpc_color_sets_noalloc gives them the statistics of bgpc_color_sets with its
 scratch in a fixed device array.  This test calls it through the C ABI twice
 in a row and checks it against bgpc_color_sets.  It lives in its own file,
