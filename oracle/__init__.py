@@ -54,8 +54,8 @@ def _load():
     G = [i32, i32, P, P, P, P]
     sig = {
         "orc_seq_color": (G + [P, i32, P], ctypes.c_int),
-        "orc_rs_color": (G + [P, i32, i32, i32, i64, i32, i64, i32, P, P, P64, P64, i32,
-                              P, P, P], ctypes.c_int),
+        "orc_rs_color": (G + [P, i32, i32, i32, i64, i32, i32, i32, i64, i32, i32, P, P,
+                              P64, P64, i32, P, P, P], ctypes.c_int),
         "orc_rs_chunks": (G + [P, P, i32, i32, i32, i64, P, i32, i32, P], ctypes.c_int),
         "orc_rs_losers": (G + [P, P, i32, P, i32, P8], ctypes.c_int),
         "orc_conflicts": (G + [P], i64),
@@ -104,8 +104,11 @@ def seq_color(g, policy: int = FF, rank=None) -> np.ndarray:
 
 def rs_color(g, policy: int = FF, chunk: int = 64, waves: int = 16, big_net: int = 64,
              rank=None, max_rounds: int = 1 << 30, stop_after_waves: int = 0,
-             nthreads: int = 1, max_report: int = 4096):
-    """O-2: round-synchronous speculative coloring RS(C, Q, T, policy, rank).
+             nthreads: int = 1, max_report: int = 4096, net_rounds: int = 0,
+             center_first: bool = False, stop_before_removal: bool = False):
+    """O-2: round-synchronous speculative coloring RS(C, Q, T, policy, rank),
+    with the first ``net_rounds`` rounds colored net by net (Alg. 8; Alg. 9
+    with ``center_first`` for D2GC's closed neighbourhoods).
 
     Returns a namespace with colors, status, rounds, w_per_round,
     trav_per_round and, when stopped, W (current work queue), m and wave."""
@@ -119,7 +122,9 @@ def rs_color(g, policy: int = FF, chunk: int = 64, waves: int = 16, big_net: int
     W = np.empty(max(n, 1), np.int32)
     r = None if rank is None else _i32(rank)
     rc = _load().orc_rs_color(*_g(g), _p(r), policy, chunk, waves, big_net, max_rounds,
-                              stop_after_waves, nthreads, _p(c), ctypes.byref(rounds),
+                              net_rounds, int(bool(center_first)), stop_after_waves,
+                              int(bool(stop_before_removal)), nthreads, _p(c),
+                              ctypes.byref(rounds),
                               _p64(wpr), _p64(tpr), max_report, _p(W), ctypes.byref(m),
                               ctypes.byref(wave))
     if rc not in (OK, STOPPED, EROUNDS, EFIXED):

@@ -327,32 +327,101 @@ static int32_t max_color(const int32_t *S, int32_t n) {
     return mx;
 }
 
-/* Conflict rule for one W position p: 1 if w loses, 0 if it keeps its color,
- * ORC_EFIXED if it shares a color with a vertex outside W. */
+/* Conflict rule for one W position p: 1 if w loses, 0 if it keeps its color.
+ * A vertex outside W sharing w's color: after a vertex-based round this
+ * cannot happen (F held that color), so it returns ORC_EFIXED unless
+ * fixed_wins is set (after a net-based round, where a net only sees its own
+ * members), in which case the fixed vertex keeps its color and w loses.  An
+ * uncolored w (no net proposed a color for it) always stays in the queue. */
 static int rs_lose_one(const int32_t *a_ptr, const int32_t *a_idx, const int32_t *b_ptr,
                        const int32_t *b_idx, const int32_t *c, const int32_t *inW,
-                       const int32_t *W, int32_t p) {
+                       const int32_t *W, int32_t p, int fixed_wins) {
     int32_t w = W[p];
+    if (c[w] < 0) return 1;
     int lose = 0;
     for (int32_t e = a_ptr[w]; e < a_ptr[w + 1]; e++) {
         int32_t v = a_idx[e];
         for (int32_t f = b_ptr[v]; f < b_ptr[v + 1]; f++) {
             int32_t u = b_idx[f];
             if (u == w || c[u] != c[w]) continue;
-            if (inW[u] < 0) return ORC_EFIXED;
-            if (inW[u] < p) lose = 1;
+            if (inW[u] < 0) {
+                if (!fixed_wins) return ORC_EFIXED;
+                lose = 1;
+            } else if (inW[u] < p) {
+                lose = 1;
+            }
         }
     }
     return lose;
 }
 
+/* ------------------------------------------------------------------------
+ * Net-based coloring round: Alg. 8 (BGPC-ColorWorkQueue-Net), and Alg. 9
+ * (D2GC-ColorWorkQueue-Net) when center_first is set, as one deterministic
+ * round.  Every net v reads the snapshot S of the round start:
+ *   F = colors of the members that are colored and not yet in F;
+ *   W_local = the other members (uncolored, or colored with a color already
+ *             in F), in adjacency order; for D2GC (nets are the closed
+ *             neighbourhoods N[v]) the center v is visited first, as Alg. 9
+ *             does before the loop over nbor(v);
+ *   reverse first fit: col starts at |vtxs(v)| - 1 (= |nbor(v)| for D2GC);
+ *   every W_local member takes the largest col not in F, then col drops by
+ *   one.
+ * In the paper every net writes its W_local members and the last writer
+ * wins; here vertex w of W takes the color proposed by its owner net own(w)
+ * (the largest net of w, ties to the larger id), the same owner as the
+ * per-vertex reverse first fit of the vertex-based rounds.  A member colored
+ * with a color already in F would be a conflict left in S, which the
+ * conflict removal never leaves: it returns ORC_EFIXED.  A W vertex without
+ * nets gets no proposal and stays uncolored.
+ * ---------------------------------------------------------------------- */
+static int rs_net_round(int32_t n_b, const int32_t *b_ptr, const int32_t *b_idx,
+                        const int32_t *own, const int32_t *inW, int center_first,
+                        const int32_t *S, fset *F, int32_t *Wl, int32_t *c) {
+    for (int32_t v = 0; v < n_b; v++) {
+        int32_t beg = b_ptr[v], end = b_ptr[v + 1], s = end - beg, nl = 0;
+        fs_clear(F);
+        int has_center = 0;
+        if (center_first)
+            for (int32_t f = beg; f < end; f++)
+                if (b_idx[f] == v) has_center = 1;
+        for (int32_t t = -1; t < s; t++) {
+            int32_t u;
+            if (t < 0) {
+                if (!has_center) continue;
+                u = v;
+            } else {
+                u = b_idx[beg + t];
+                if (has_center && u == v) continue;
+            }
+            if (S[u] != -1 && !fs_has(F, S[u])) {
+                fs_add(F, S[u]);
+            } else {
+                if (S[u] != -1) return ORC_EFIXED;
+                Wl[nl++] = u;
+            }
+        }
+        int32_t col = s - 1;
+        for (int32_t i = 0; i < nl; i++) {
+            while (fs_has(F, col)) col--;
+            if (col < 0) return ORC_EINVAL;  /* at least |W_local| colors are free */
+            int32_t u = Wl[i];
+            if (inW[u] >= 0 && own[u] == v) c[u] = col;
+            col--;
+        }
+    }
+    return ORC_OK;
+}
+
 int orc_rs_color(int32_t n_a, int32_t n_b, const int32_t *a_ptr, const int32_t *a_idx,
                  const int32_t *b_ptr, const int32_t *b_idx, const int32_t *rank,
                  int32_t policy, int32_t C, int32_t Q, int64_t T, int32_t max_rounds,
-                 int64_t stop_after_waves, int32_t nthreads, int32_t *c,
+                 int32_t net_rounds, int32_t center_first, int64_t stop_after_waves,
+                 int32_t stop_before_removal, int32_t nthreads, int32_t *c,
                  int32_t *rounds_out, int64_t *w_per_round, int64_t *trav_per_round,
                  int32_t max_report, int32_t *W_out, int32_t *m_out, int32_t *wave_out) {
-    if (n_a < 0 || C < 1 || Q < 1 || !valid_policy(policy)) return ORC_EINVAL;
+    if (n_a < 0 || C < 1 || Q < 1 || net_rounds < 0 || !valid_policy(policy)) return ORC_EINVAL;
+    if (center_first && n_a != n_b) return ORC_EINVAL;
     if (nthreads < 1) nthreads = 1;
     if (nthreads > 256) nthreads = 256;
     size_t na = (size_t)n_a + 1;
@@ -369,8 +438,9 @@ int orc_rs_color(int32_t n_a, int32_t n_b, const int32_t *a_ptr, const int32_t *
     int64_t *wlist = (int64_t *)malloc(sizeof(int64_t) * na);
     rs_worker *wk = (rs_worker *)calloc((size_t)nthreads, sizeof(rs_worker));
     int rc = ORC_OK;
+    int32_t *Wl = (int32_t *)malloc(sizeof(int32_t) * na);
     if (!W || !Wn || !inW || !own || !s_own || !k || !S || !out || !lose || !wk || !woff || !wlist ||
-        alloc_workers(wk, nthreads, n_a)) {
+        !Wl || alloc_workers(wk, nthreads, n_a)) {
         rc = ORC_ENOMEM;
         goto done;
     }
@@ -382,22 +452,49 @@ int orc_rs_color(int32_t n_a, int32_t n_b, const int32_t *a_ptr, const int32_t *
     int64_t waves_done = 0;
     while (m > 0) {
         if (r >= max_rounds) { rc = ORC_EROUNDS; break; }
+        const int net = r < net_rounds;
+        for (int32_t p = 0; p < m; p++) inW[W[p]] = p;
         if (r < max_report) {
+            /* vertex round: the two-hop entries the vertices of W read;
+             * net round: the members of the nets touching W, read once */
             int64_t trav = 0;
-            for (int32_t p = 0; p < m; p++) {
-                int32_t w = W[p];
-                for (int32_t e = a_ptr[w]; e < a_ptr[w + 1]; e++) {
-                    int32_t v = a_idx[e];
-                    trav += b_ptr[v + 1] - b_ptr[v] - 1;
+            if (net) {
+                for (int32_t v = 0; v < n_b; v++) {
+                    int touch = 0;
+                    for (int32_t f = b_ptr[v]; f < b_ptr[v + 1] && !touch; f++)
+                        touch = inW[b_idx[f]] >= 0;
+                    if (touch) trav += b_ptr[v + 1] - b_ptr[v];
+                }
+            } else {
+                for (int32_t p = 0; p < m; p++) {
+                    int32_t w = W[p];
+                    for (int32_t e = a_ptr[w]; e < a_ptr[w + 1]; e++) {
+                        int32_t v = a_idx[e];
+                        trav += b_ptr[v + 1] - b_ptr[v] - 1;
+                    }
                 }
             }
             if (w_per_round) w_per_round[r] = m;
             if (trav_per_round) trav_per_round[r] = trav;
         }
         r++;
-        for (int32_t p = 0; p < m; p++) inW[W[p]] = p;
-        reverse_offsets(n_b, b_ptr, b_idx, own, inW, T, k);
         memcpy(S, c, sizeof(int32_t) * (size_t)n_a);
+        if (net) {
+            /* a net round counts as one wave for stop_after_waves */
+            if (stop_after_waves > 0 && waves_done == stop_after_waves) {
+                if (W_out) memcpy(W_out, W, sizeof(int32_t) * (size_t)m);
+                if (m_out) *m_out = m;
+                if (wave_out) *wave_out = 0;
+                if (rounds_out) *rounds_out = r;
+                rc = ORC_STOPPED;
+                goto done;
+            }
+            if ((rc = rs_net_round(n_b, b_ptr, b_idx, own, inW, center_first, S, &wk[0].F, Wl,
+                                   c)) != ORC_OK)
+                goto done;
+            waves_done++;
+        } else {
+        reverse_offsets(n_b, b_ptr, b_idx, own, inW, T, k);
 
         rs_ctx x;
         x.n_a = n_a; x.a_ptr = a_ptr; x.a_idx = a_idx; x.b_ptr = b_ptr; x.b_idx = b_idx;
@@ -426,11 +523,21 @@ int orc_rs_color(int32_t n_a, int32_t n_b, const int32_t *a_ptr, const int32_t *
             waves_done++;
         }
         memcpy(c, S, sizeof(int32_t) * (size_t)n_a);
+        }
+        if (stop_before_removal && stop_after_waves > 0 && waves_done == stop_after_waves) {
+            if (W_out) memcpy(W_out, W, sizeof(int32_t) * (size_t)m);
+            if (m_out) *m_out = m;
+            if (wave_out) *wave_out = net ? 1 : Q;
+            if (rounds_out) *rounds_out = r;
+            rc = ORC_STOPPED;
+            goto done;
+        }
 
-        /* RemoveConflicts (Alg. 3/5 rule, lower rank wins) */
+        /* RemoveConflicts (Alg. 3/5 rule, lower rank wins; after a net round
+         * a fixed vertex also wins) */
         int32_t mn = 0;
         for (int32_t p = 0; p < m; p++) {
-            int l = rs_lose_one(a_ptr, a_idx, b_ptr, b_idx, c, inW, W, p);
+            int l = rs_lose_one(a_ptr, a_idx, b_ptr, b_idx, c, inW, W, p, net);
             if (l == ORC_EFIXED) { rc = ORC_EFIXED; goto done; }
             lose[p] = (uint8_t)l;
         }
@@ -448,7 +555,7 @@ int orc_rs_color(int32_t n_a, int32_t n_b, const int32_t *a_ptr, const int32_t *
 done:
     if (wk) free_workers(wk, nthreads);
     free(wk); free(W); free(Wn); free(inW); free(own); free(s_own); free(k);
-    free(S); free(out); free(lose); free(woff); free(wlist);
+    free(S); free(out); free(lose); free(woff); free(wlist); free(Wl);
     return rc;
 }
 
@@ -508,7 +615,7 @@ int orc_rs_losers(int32_t n_a, int32_t n_b, const int32_t *a_ptr, const int32_t 
     for (int32_t p = 0; p < m; p++) inW[W[p]] = p;
     int rc = ORC_OK;
     for (int32_t i = 0; i < nwhich; i++) {
-        int l = rs_lose_one(a_ptr, a_idx, b_ptr, b_idx, c, inW, W, which[i]);
+        int l = rs_lose_one(a_ptr, a_idx, b_ptr, b_idx, c, inW, W, which[i], 0);
         if (l == ORC_EFIXED) { rc = ORC_EFIXED; l = 1; }
         lose[i] = (uint8_t)l;
     }

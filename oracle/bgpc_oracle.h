@@ -41,16 +41,25 @@ int orc_seq_color(int32_t n_a, int32_t n_b, const int32_t *a_ptr, const int32_t 
  * lower-rank-wins conflict removal.  Chunk j (C consecutive work-queue
  * entries) belongs to wave ((j * 0x9E3779B9 mod 2^32) * Q) >> 32.  nthreads > 1 colors the chunks of a wave
  * on several host threads (results do not depend on it).
- * stop_after_waves > 0 stops after that many waves (counted over all rounds)
- * and returns ORC_STOPPED with c = the snapshot at that point, W_out (if not
- * NULL) = the current round's work queue in rank order, *m_out = its length
- * and *wave_out = the index, within its round, of the next wave.
+ * The first net_rounds rounds are net-based instead (Alg. 8 as one
+ * round-synchronous round: every net reads the round's snapshot and proposes
+ * reverse first-fit colors for its uncolored members, every vertex takes its
+ * owner net's proposal, and a vertex outside W wins a clash; center_first:
+ * Alg. 9's order for D2GC, where net v is N[v] and v is visited first).
+ * stop_after_waves > 0 stops after that many waves (counted over all rounds;
+ * a net round counts as one wave) and returns ORC_STOPPED with c = the
+ * snapshot at that point, W_out (if not NULL) = the current round's work
+ * queue in rank order, *m_out = its length and *wave_out = the index, within
+ * its round, of the next wave; with stop_before_removal, a stop that lands on
+ * the end of a round comes before its conflict removal (c = the tentative
+ * colors, *wave_out = the round's wave count).
  * Per-round |W_r| and traversed two-hop entries go to w_per_round /
  * trav_per_round (first max_report rounds; NULL to skip). */
 int orc_rs_color(int32_t n_a, int32_t n_b, const int32_t *a_ptr, const int32_t *a_idx,
                  const int32_t *b_ptr, const int32_t *b_idx, const int32_t *rank,
                  int32_t policy, int32_t C, int32_t Q, int64_t T, int32_t max_rounds,
-                 int64_t stop_after_waves, int32_t nthreads, int32_t *c,
+                 int32_t net_rounds, int32_t center_first, int64_t stop_after_waves,
+                 int32_t stop_before_removal, int32_t nthreads, int32_t *c,
                  int32_t *rounds, int64_t *w_per_round, int64_t *trav_per_round,
                  int32_t max_report, int32_t *W_out, int32_t *m_out, int32_t *wave_out);
 

@@ -59,8 +59,12 @@ def update(pol, col, state):
         state["col_next"] = max(col + 1, state["col_max"] // 3 + 1)
 
 
-def rs(n_a, nets, pol=0, C=64, Q=16, T=64, rank=None, max_rounds=10_000):
-    """nets: list of member lists (vtxs).  Returns (colors, w_per_round)."""
+def rs(n_a, nets, pol=0, C=64, Q=16, T=64, rank=None, max_rounds=10_000, net_rounds=0,
+       center_first=False):
+    """nets: list of member lists (vtxs).  Returns (colors, w_per_round).
+    The first net_rounds rounds are net-based (Alg. 8 / Alg. 9): each net
+    proposes reverse first-fit colors to its uncolored members, read from the
+    round's snapshot, and each vertex keeps its owner net's proposal."""
     vtxs_of = [sorted(set(m)) for m in nets]
     nets_of = [[] for _ in range(n_a)]
     for v, mem in enumerate(vtxs_of):
@@ -98,7 +102,24 @@ def rs(n_a, nets, pol=0, C=64, Q=16, T=64, rank=None, max_rounds=10_000):
         S = list(c)
         m = len(W)
         nch = (m + C - 1) // C
-        for q in range(Q):
+        net_round = len(hist) <= net_rounds
+        if net_round:
+            for v, mem in enumerate(vtxs_of):
+                visit = list(mem)
+                if center_first and v in visit:
+                    visit.remove(v)
+                    visit.insert(0, v)
+                F, todo = set(), []
+                for u in visit:
+                    if S[u] != -1 and S[u] not in F:
+                        F.add(S[u])
+                    else:
+                        todo.append(u)
+                free = [x for x in range(len(mem) - 1, -1, -1) if x not in F]
+                for i, u in enumerate(todo):
+                    if own[u] == v and u in pos:
+                        c[u] = free[i]
+        for q in range(0 if net_round else Q):
             staged = {}
             for j in [j for j in range(nch) if wave_of(j, Q) == q]:
                 L = {}
@@ -121,14 +142,15 @@ def rs(n_a, nets, pol=0, C=64, Q=16, T=64, rank=None, max_rounds=10_000):
                     staged[w] = col
             for w, col in staged.items():
                 S[w] = col
-        c = S
+        if not net_round:
+            c = S
         losers = []
         for p, w in enumerate(W):
-            lose = False
+            lose = c[w] < 0
             for u in nb[w]:
-                if c[u] == c[w]:
-                    assert u in pos, "a W vertex took a fixed neighbour's color"
-                    if pos[u] < p:
+                if c[u] == c[w] and c[w] >= 0:
+                    assert net_round or u in pos, "a W vertex took a fixed neighbour's color"
+                    if u not in pos or pos[u] < p:
                         lose = True
             if lose:
                 losers.append(w)

@@ -410,3 +410,106 @@ def test_d2_conflicts_hand_counts():
     assert O.d2_conflicts(ug, [0, 0, 1, 2]) == 2   # adjacent clash
     assert O.d2_conflicts(ug, [0, 1, -1, 0]) == 1  # uncolored
     assert O.d2_conflicts(ug, [0, 0, 0, 0]) == 4
+
+
+# ------------------------------------------------------- net-based rounds
+#
+# Alg. 8 / Alg. 9 as the first round(s) of the N1-N2 / N2-N2 schedules of
+# Sec. VI: every net reads the round's snapshot and proposes reverse
+# first-fit colors to its uncolored members, every vertex keeps its owner
+# net's proposal, a fixed vertex wins a clash.
+
+def test_net_round_golden():
+    fx = golden("rs_net_round.json")
+    for key in ("path", "single_net"):
+        case = fx[key]
+        g = gg.from_nets(case["n_a"], case["nets"])
+        r = O.rs_color(g, net_rounds=1)
+        assert r.status == O.OK
+        assert r.colors.tolist() == case["expected"]
+        assert r.w_per_round.tolist() == case["w_per_round"]
+        c_py, hist = rs_py.rs(case["n_a"], case["nets"], net_rounds=1)
+        assert c_py == case["expected"] and hist == case["w_per_round"]
+    st = fx["star_center_2"]
+    cn = O.closed_nbhd(gg.from_edges(st["n"], st["edges"]))
+    assert O.rs_color(cn, net_rounds=1, center_first=True).colors.tolist() == \
+        st["expected_center_first"]
+    assert O.rs_color(cn, net_rounds=1).colors.tolist() == st["expected_adjacency_order"]
+
+
+def owner_nets(g):
+    own = np.full(g.n_a, -1, np.int64)
+    sizes = np.diff(g.b_ptr)
+    for w in range(g.n_a):
+        nets = g.a_idx[g.a_ptr[w]:g.a_ptr[w + 1]]
+        if len(nets):
+            own[w] = max(nets, key=lambda v: (sizes[v], v))
+    return own
+
+
+@pytest.mark.parametrize("center_first", [False, True])
+def test_net_round_proposals_per_net(center_first):
+    """Before its conflict removal, a net round gives the members that own a
+    net distinct colors below |vtxs(v)| (the reverse first fit from
+    |vtxs(v)| - 1 never reuses a color within a net and never goes below 0),
+    and leaves exactly the vertices without nets uncolored."""
+    rng = np.random.default_rng(41)
+    for it in range(12):
+        if center_first:
+            ug = gg.rmat(7, 4, seed=60 + it)
+            g = O.closed_nbhd(ug)
+        else:
+            g = gg.random_bipartite(300, 120, 3, seed=60 + it)
+        r = O.rs_color(g, net_rounds=1, center_first=center_first, stop_after_waves=1,
+                       stop_before_removal=True)
+        assert r.status == O.STOPPED and r.wave == 1 and r.m == g.n_a
+        own = owner_nets(g)
+        c = r.colors
+        assert np.array_equal(c < 0, own < 0)
+        sizes = np.diff(g.b_ptr)
+        for v in range(g.n_b):
+            mem = g.b_idx[g.b_ptr[v]:g.b_ptr[v + 1]]
+            owned = c[mem[own[mem] == v]]
+            assert len(set(owned.tolist())) == len(owned)
+            assert np.all((owned >= 0) & (owned < sizes[v]))
+
+
+@pytest.mark.parametrize("net_rounds", [1, 2, 3])
+def test_net_rounds_valid_and_match_python(net_rounds):
+    """Colorings with net-based leading rounds are valid (Sec. II), every
+    vertex-based round after them keeps the usual invariants, and the C
+    oracle equals the independent Python statement, for all policies and
+    ranks (the net round itself uses the reverse first fit whatever the
+    policy)."""
+    rng = np.random.default_rng(43 + net_rounds)
+    for it in range(25):
+        n_a, n_b = int(rng.integers(1, 40)), int(rng.integers(1, 25))
+        g, nets = random_tiny(rng, n_a, n_b, 7)
+        pol = POLICIES[it % 4]
+        C, Q, T = int(rng.integers(1, 9)), int(rng.integers(1, 5)), int(rng.integers(0, 6))
+        rank = rng.permutation(n_a).astype(np.int32) if it % 3 == 0 else None
+        r = O.rs_color(g, pol, chunk=C, waves=Q, big_net=T, rank=rank, net_rounds=net_rounds)
+        assert r.status == O.OK
+        assert O.conflicts(g, r.colors) == 0
+        c_py, hist = rs_py.rs(n_a, nets, pol, C, Q, T, None if rank is None else rank.tolist(),
+                              net_rounds=net_rounds)
+        assert r.colors.tolist() == c_py and r.w_per_round.tolist() == hist
+
+
+def test_net_round_traversal_is_linear():
+    """A net round reads every net touching W once: sum of |vtxs(v)| = nnz
+    in the first round (every net has a member in W_0)."""
+    g = gg.random_bipartite(500, 300, 4, seed=3)
+    r = O.rs_color(g, net_rounds=1)
+    sizes = np.diff(g.b_ptr)
+    assert r.trav_per_round[0] == int(sizes[sizes > 0].sum()) == g.nnz
+    r0 = O.rs_color(g)
+    assert r0.trav_per_round[0] == int((sizes * (sizes - 1)).sum())
+
+
+def test_net_round_d2gc_valid_by_distance():
+    ug = gg.rmat(9, 8, seed=5)
+    cn = O.closed_nbhd(ug)
+    for pol in POLICIES:
+        r = O.rs_color(cn, pol, chunk=8, waves=4, big_net=16, net_rounds=1, center_first=True)
+        assert r.status == O.OK and O.d2_conflicts(ug, r.colors) == 0
