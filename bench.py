@@ -443,12 +443,43 @@ def d2gc_report(bg, ctx, dev, steps: int, warmup: int, records):
                "colors_vs_seq": st["colors"] / seq["colors"] if seq else None,
                "seq_balance": seq}
         out["policies"][name] = rec
+    out["schedules"] = schedule_report(bg, ctx, [dug], [ug], steps, records, d2=True)[0]
     ff = out["policies"]["FF"]
     for name in ("B1", "B2"):
         r = out["policies"][name]
         r["vs_FF"] = {"colors": r["n_sets"] / ff["n_sets"], "mean_card": r["mean_card"] / ff["mean_card"],
                       "std_card": r["std_card"] / ff["std_card"] if ff["std_card"] else None,
                       "time": r["ms"] / ff["ms"]}
+    return out
+
+
+def schedule_report(bg, ctx, dgs, graphs, steps: int, records, d2=False):
+    """The schedules of Sec. VI side by side on the same graphs: V-* (every
+    round vertex-based, the timed configuration) and N1-* (the first round
+    net-based, Alg. 8 / Alg. 9), each a complete coloring timed with CUDA
+    events: time, rounds, colors, traversal over E2 and E2 per second."""
+    import torch
+    stream = torch.cuda.current_stream()
+    out = []
+    for g, dg in zip(graphs, dgs):
+        e2 = e2_of(g)
+        rec = {"graph": g.name}
+        for name, nr in (("V", 0), ("N1", 1)):
+            fn = (lambda: bg.d2gc_color(ctx, dg, net_rounds=nr)) if d2 else \
+                 (lambda: bg.bgpc_color(ctx, dg, net_rounds=nr))
+            fn()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for _ in range(steps):
+                _, st, _ = fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / steps
+            rec[name] = {"ms": ms, "rounds": st["rounds"], "colors": st["colors"],
+                         "w_per_round": st["w_per_round"][:8],
+                         "trav_over_E2": st["trav_total"] / e2, "E2_per_s": e2 / (ms / 1000.0)}
+        out.append(rec)
     return out
 
 
@@ -603,6 +634,10 @@ def run_gpu(args):
     if rank == 0 and jac and not args.no_d2gc:
         d2gc = d2gc_report(bg, ctx, dev, steps=3, warmup=1, records=records)
 
+    schedules = None
+    if rank == 0 and jac:
+        schedules = schedule_report(bg, ctx, dgs, graphs, 3, records)
+
     learned = None
     if rank == 0 and not args.no_learned and jac:
         learned = learned_order_report(bg, ctx, dev, dgs[1])
@@ -674,6 +709,7 @@ def run_gpu(args):
             "gpu_launches": launches,
             "cpu_baseline": cpu,
             "clocks": clocks,
+            "schedules": schedules,
             "d2gc_rmat22": d2gc,
             "learned_order": learned,
         }

@@ -112,10 +112,11 @@ typedef struct {
                                 a CTA's shared memory, else one CTA per piece) or
                                 BGPC_GATHER_CTA (1: always one CTA per piece); a
                                 mapping parameter, results do not change */
-    int32_t net_rounds;      /* semantic: the first net_rounds rounds are colored net by
-                                net (Alg. 8; Alg. 9 for D2GC) instead of by vertex
-                                waves: 0 = V-* (default), 1 = N1-*, 2 = N2-* of Sec. VI;
-                                see bgpc_color */
+    int32_t net_rounds;      /* semantic: 1 colors the first round net by net (Alg. 8;
+                                Alg. 9's order for D2GC) instead of by vertex waves,
+                                the N1-* schedules of Sec. VI; 0 (default) = V-*.
+                                A net round counts as one wave for stop_after_waves.
+                                Other values: BGPC_EINVAL (see bgpc_color) */
     int64_t timeout_us;      /* > 0: wall-clock limit of the call in microseconds,
                                 checked each time the host waits for the device (after
                                 the setup and after every round); when exceeded the
@@ -167,6 +168,14 @@ int bgpc_ctx_destroy(bgpc_ctx_t *ctx);
 /* BGPC (Sec. III; Alg. 1 round loop, Alg. 4 vertex-based two-hop gather,
  * Alg. 8 reverse first fit for big nets, Alg. 7 net-based conflict removal
  * with the Alg. 3 lower-rank-wins rule, Sec. V balancing).
+ * With opts.net_rounds = 1 the first round is Alg. 8's net-based coloring:
+ * every net proposes the colors |vtxs(v)| - 1, |vtxs(v)| - 2, ... to its
+ * members in adjacency order (all are uncolored, so F is empty), every
+ * vertex keeps the proposal of its owner net (its largest net, ties to the
+ * larger id, standing for the paper's last writer) and a vertex without nets
+ * stays uncolored for the next round; the conflict removal and the later
+ * vertex-based rounds are unchanged.  The net round reads nnz entries instead
+ * of the two-hop volume; it uses reverse first fit whatever opts.policy.
  * colors: device int32 [n_a], written on BGPC_OK (or the snapshot on
  * BGPC_STOPPED).  stats (host) may be NULL.  Synchronises `stream`. */
 int bgpc_color(bgpc_ctx_t *ctx, const bgpc_graph_t *g, const bgpc_opts_t *opts,

@@ -79,7 +79,9 @@ int check_opts(const bgpc_opts_t *o) {
   if (o->chunk < 1 || o->chunk > kMaxChunk) return BGPC_EINVAL;
   if (o->waves < 1 || o->big_net < 0 || o->max_rounds < 1 || o->stop_after_waves < 0)
     return BGPC_EINVAL;
-  if (o->net_rounds != 0 || o->timeout_us < 0) return BGPC_EINVAL;
+  // net-based coloring is built for the first round (N1-*), where every
+  // vertex is uncolored; later net rounds (N2-*) are not
+  if (o->net_rounds < 0 || o->net_rounds > 1 || o->timeout_us < 0) return BGPC_EINVAL;
   return BGPC_OK;
 }
 
@@ -154,8 +156,11 @@ int ensure_table(bgpc_ctx_t *ctx, size_t entries, cudaStream_t s, int64_t *nk) {
   return BGPC_OK;
 }
 
+// center_first: the nets are D2GC's closed neighbourhoods (net v = N[v]),
+// and a net-based round visits the center v first (Alg. 9).
 int color_impl(bgpc_ctx_t *ctx, const bgpc_graph_t &g, const bgpc_opts_t &o, int32_t *colors,
-               bgpc_stats_t *stats, cudaStream_t s, const Deadline &dl) {
+               bgpc_stats_t *stats, cudaStream_t s, const Deadline &dl,
+               int32_t center_first = 0) {
   bgpc_stats_t st;
   memset(&st, 0, sizeof(st));
   const int32_t n_a = g.n_a, n_b = g.n_b, nnz = g.nnz;
@@ -189,6 +194,7 @@ int color_impl(bgpc_ctx_t *ctx, const bgpc_graph_t &g, const bgpc_opts_t &o, int
   CU(grow(ctx->bigd, (size_t)(n_b > 0 ? n_b : 1)));
   CU(grow(ctx->hub_id, (size_t)(n_b > 0 ? n_b : 1)));
   CU(grow(ctx->hub_net, (size_t)nnz / (kHubMin + 1) + 1));
+  if (o.net_rounds > 0) CU(grow(ctx->netc, (size_t)n_a));
 
   // ---- setup (Alg. 1: W <- V_color, c <- -1), static graph analysis
   PhaseTimer tm(ctx, s, o.profile != 0);
@@ -198,7 +204,8 @@ int color_impl(bgpc_ctx_t *ctx, const bgpc_graph_t &g, const bgpc_opts_t &o, int
   CU(cudaMemsetAsync(&ctx->dev->gmax, 0xff, sizeof(int32_t), s));
   CU(cudaMemsetAsync(ctx->lose.p, 0, (size_t)n_a, s));
   nk += launch_tpos(g, ctx->tpos.p, &ctx->dev->err, sms, s);
-  nk += launch_vertex_static(g, ctx->tpos.p, ctx->s_own.p, ctx->d2tot.p, ctx->nown.p, sms, s);
+  nk += launch_vertex_static(g, ctx->tpos.p, ctx->s_own.p, ctx->d2tot.p, ctx->nown.p,
+                             o.net_rounds > 0 ? ctx->netc.p : nullptr, center_first, sms, s);
   nk += launch_net_static(g, o.big_net, ctx->bigt.p, ctx->bigd.p, ctx->dev, s);
   nk += launch_hub_select(g.b_ptr, n_b, kHubMin, ctx->hub_id.p, ctx->hub_net.p, ctx->dev, sms, s);
   nk += launch_init_queue(o.rank, n_a, ctx->W0.p, &ctx->dev->err, s);
@@ -233,6 +240,29 @@ int color_impl(bgpc_ctx_t *ctx, const bgpc_graph_t &g, const bgpc_opts_t &o, int
     const int32_t nslots = nbig_d < 2 * sms ? (nbig_d > 0 ? nbig_d : 1) : 2 * sms;
     if ((rc = ensure_table(ctx, (size_t)nslots * (size_t)cbw, s, &nk))) return rc;
 
+    const bool net = r < o.net_rounds;
+    if (net) {
+      // ---- net-based coloring round (Alg. 8 / Alg. 9): every vertex takes
+      // its owner net's reverse first-fit proposal, computed in the setup;
+      // it counts as one wave
+      if (o.stop_after_waves > 0 && waves_done == o.stop_after_waves) {
+        if (o.W_out) CU(cudaMemcpyAsync(o.W_out, W, sizeof(int32_t) * (size_t)m,
+                                        cudaMemcpyDeviceToDevice, s));
+        CU(cudaStreamSynchronize(s));
+        tm.collect();
+        st.rounds = r + 1;
+        st.stopped_m = m;
+        st.stopped_wave = 0;
+        st.colors = gmax + 1;
+        if (stats) *stats = st;
+        return BGPC_STOPPED;
+      }
+      CU(cudaMemsetAsync(&ctx->dev->trav, 0, kRoundCounters * sizeof(unsigned long long), s));
+      ev = tm.begin();
+      nk += launch_net_publish(g, ctx->netc.p, o.rank, ctx->nc.p, colors, ctx->lose.p, sms, s);
+      tm.end(ev, PH_COLOR);
+      waves_done++;
+    } else {
     ev = tm.begin();
     if (nbig_t > 0)
       nk += launch_kofs(g.b_ptr, ctx->nc.p, ctx->npos.p, ctx->nown.p, ctx->bigt.p, nbig_t,
@@ -377,6 +407,7 @@ int color_impl(bgpc_ctx_t *ctx, const bgpc_graph_t &g, const bgpc_opts_t &o, int
       }
       waves_done++;
     }
+    }  // vertex-based round
     if (o.stop_before_removal && o.stop_after_waves > 0 && waves_done == o.stop_after_waves) {
       if (o.W_out) CU(cudaMemcpyAsync(o.W_out, W, sizeof(int32_t) * (size_t)m,
                                       cudaMemcpyDeviceToDevice, s));
@@ -384,7 +415,7 @@ int color_impl(bgpc_ctx_t *ctx, const bgpc_graph_t &g, const bgpc_opts_t &o, int
       tm.collect();
       st.rounds = r + 1;
       st.stopped_m = m;
-      st.stopped_wave = Q;
+      st.stopped_wave = net ? 1 : Q;
       if (stats) *stats = st;
       return BGPC_STOPPED;
     }
@@ -425,12 +456,15 @@ int color_impl(bgpc_ctx_t *ctx, const bgpc_graph_t &g, const bgpc_opts_t &o, int
       return err_to_status(ctx->host->err);
     }
     if (dl.passed()) return BGPC_ETIMEOUT;
+    // a net round reads every net touching W once: all of them in the
+    // first round, sum of |vtxs(v)| = nnz entries and incidences
+    const int64_t trav_r = net ? (int64_t)nnz : (int64_t)ctx->host->trav;
     if (r < BGPC_MAX_REPORT) {
       st.w_per_round[r] = m;
-      st.trav_per_round[r] = (int64_t)ctx->host->trav;
+      st.trav_per_round[r] = trav_r;
     }
-    st.trav_total += (int64_t)ctx->host->trav;
-    st.incid_total += (int64_t)ctx->host->incid;
+    st.trav_total += trav_r;
+    st.incid_total += net ? (int64_t)nnz : (int64_t)ctx->host->incid;
     st.trav_large += (int64_t)ctx->host->trav_large;
     st.incid_large += (int64_t)ctx->host->incid_large;
     st.w_large += (int64_t)ctx->host->w_large;
@@ -527,6 +561,7 @@ int bgpc_ctx_destroy(bgpc_ctx_t *ctx) {
   release(ctx->tpos); release(ctx->nc); release(ctx->npos); release(ctx->nown);
   release(ctx->s_own); release(ctx->d2tot); release(ctx->W0); release(ctx->W1);
   release(ctx->kofs); release(ctx->stage); release(ctx->newpos); release(ctx->lose);
+  release(ctx->netc);
   release(ctx->blocksum); release(ctx->bigt); release(ctx->bigd);
   release(ctx->hub_id); release(ctx->hub_net); release(ctx->nbm);
   release(ctx->cptr); release(ctx->cidx); release(ctx->dtab); release(ctx->vtab);
@@ -690,7 +725,7 @@ int d2gc_color(bgpc_ctx_t *ctx, const bgpc_ugraph_t *g, const bgpc_opts_t *opts,
   bg.b_ptr = ctx->cptr.p;
   bg.b_idx = ctx->cidx.p;
   bgpc_opts_t o = *opts;
-  return color_impl(ctx, bg, o, colors, stats, s, dl);
+  return color_impl(ctx, bg, o, colors, stats, s, dl, 1);
 }
 
 int bgpc_validate(bgpc_ctx_t *ctx, const bgpc_graph_t *g, const int32_t *colors, int64_t *n_bad,

@@ -92,6 +92,7 @@ struct bgpc_ctx {
   bgpc::Buf<int32_t> tpos, nc, npos;
   bgpc::Buf<uint8_t> nown;
   bgpc::Buf<int32_t> s_own, d2tot, W0, W1, kofs, stage, newpos;
+  bgpc::Buf<int32_t> netc;             // net-based first round: proposal of the owner net
   bgpc::Buf<uint8_t> lose;
   bgpc::Buf<int32_t> blocksum, bigt, bigd;
   bgpc::Buf<int32_t> wlist;            // chunks of the round ordered by wave
@@ -158,7 +159,12 @@ int launch_check_rows(const int32_t *ptr, const int32_t *idx, int32_t n, int32_t
                        int32_t *err, int sms, cudaStream_t s);
 int launch_tpos(const bgpc_graph_t &g, int32_t *tpos, int32_t *err, int sms, cudaStream_t s);
 int launch_vertex_static(const bgpc_graph_t &g, const int32_t *tpos, int32_t *s_own,
-                          int32_t *d2tot, uint8_t *nown, int sms, cudaStream_t s);
+                          int32_t *d2tot, uint8_t *nown, int32_t *netc, int32_t center_first,
+                          int sms, cudaStream_t s);
+// The net-based first round (Alg. 8 / Alg. 9): its colors, computed by
+// launch_vertex_static into netc, published into c and the mirror.
+int launch_net_publish(const bgpc_graph_t &g, const int32_t *netc, const int32_t *rank,
+                       int32_t *nc, int32_t *colors, uint8_t *lose, int sms, cudaStream_t s);
 int launch_net_static(const bgpc_graph_t &g, int32_t T, int32_t *bigt, int32_t *bigd,
                        DevScalars *dev, cudaStream_t s);
 int launch_init_queue(const int32_t *rank, int32_t n_a, int32_t *W, int32_t *err, cudaStream_t s);

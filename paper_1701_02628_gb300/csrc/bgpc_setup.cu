@@ -98,12 +98,20 @@ __global__ void k_tpos(const int32_t *__restrict__ a_ptr, const int32_t *__restr
 // Per vertex: owner net (largest, ties -> larger id), its size, the sum of
 // its net sizes (two-hop volume incl. w itself), and the owner flag nown[]
 // of every CSC entry.
+// With netc != NULL also the color the net-based first round (Alg. 8) gives
+// w: in that round every vertex is uncolored, so F is empty in every net and
+// the i-th visited member of net v is proposed |vtxs(v)| - 1 - i; w keeps
+// the proposal of its owner net, where it sits at CSC position tpos of its
+// owner entry (i = that position within the net; with center_first, Alg. 9's
+// order for D2GC, the center v is visited first and the others follow in
+// adjacency order).  A vertex without nets gets -1.
 __global__ void k_vertex_static(const int32_t *__restrict__ a_ptr,
                                 const int32_t *__restrict__ a_idx,
                                 const int32_t *__restrict__ b_ptr,
                                 const int32_t *__restrict__ tpos, int32_t n_a,
                                 int32_t *__restrict__ s_own, int32_t *__restrict__ d2tot,
-                                uint8_t *__restrict__ nown) {
+                                uint8_t *__restrict__ nown, int32_t *__restrict__ netc,
+                                int32_t center_first) {
   const int lane = threadIdx.x & 31;
   int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -125,11 +133,22 @@ __global__ void k_vertex_static(const int32_t *__restrict__ a_ptr,
       if (ob > best) best = ob;
     }
     int32_t own = (end > beg) ? (int32_t)(best & 0xffffffffu) : -1;
+    const int32_t so = (end > beg) ? (int32_t)(best >> 32) : 0;
     if (lane == 0) {
-      s_own[w] = (end > beg) ? (int32_t)(best >> 32) : 0;
+      s_own[w] = so;
       d2tot[w] = (int32_t)sum;
+      if (netc && end == beg) netc[w] = -1;
     }
-    for (int32_t i = beg + lane; i < end; i += 32) nown[tpos[i]] = (a_idx[i] == own) ? 1 : 0;
+    for (int32_t i = beg + lane; i < end; i += 32) {
+      const bool mine = a_idx[i] == own;
+      const int32_t f = tpos[i];
+      nown[f] = mine ? 1 : 0;
+      if (netc && mine) {
+        int32_t k = f - b_ptr[own];
+        if (center_first) k = ((int32_t)w == own) ? 0 : k + 1 - (own < (int32_t)w ? 1 : 0);
+        netc[w] = so - 1 - k;
+      }
+    }
   }
 }
 
@@ -246,10 +265,41 @@ int launch_tpos(const bgpc_graph_t &g, int32_t *tpos, int32_t *err, int sms, cud
 }
 
 int launch_vertex_static(const bgpc_graph_t &g, const int32_t *tpos, int32_t *s_own,
-                          int32_t *d2tot, uint8_t *nown, int sms, cudaStream_t s) {
+                          int32_t *d2tot, uint8_t *nown, int32_t *netc, int32_t center_first,
+                          int sms, cudaStream_t s) {
   if (g.n_a <= 0) return 0;
   k_vertex_static<<<grid_warps(g.n_a, sms), kNT, 0, s>>>(g.a_ptr, g.a_idx, g.b_ptr, tpos,
-                                                          g.n_a, s_own, d2tot, nown);
+                                                          g.n_a, s_own, d2tot, nown, netc,
+                                                          center_first);
+  return 1;
+}
+
+// The net-based first round's colors (netc, from k_vertex_static) become the
+// round's tentative coloring: c[w] = netc[w], mirrored into every CSC entry
+// (nc[f] = netc[b_idx[f]], written in CSC order); a vertex without nets got
+// no proposal and is flagged to stay in the work queue (it has no CSC entry,
+// so the conflict removal never sees it).
+__global__ void k_net_publish(const int32_t *__restrict__ b_idx, int64_t nnz,
+                              const int32_t *__restrict__ netc, const int32_t *__restrict__ rank,
+                              int32_t n_a, int32_t *__restrict__ nc,
+                              int32_t *__restrict__ colors, uint8_t *__restrict__ lose) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; f < nnz; f += stride)
+    nc[f] = netc[b_idx[f]];
+  for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < n_a; w += stride) {
+    const int32_t c = netc[w];
+    colors[w] = c;
+    if (c < 0) lose[rank ? rank[w] : (int32_t)w] = 1;
+  }
+}
+
+int launch_net_publish(const bgpc_graph_t &g, const int32_t *netc, const int32_t *rank,
+                       int32_t *nc, int32_t *colors, uint8_t *lose, int sms, cudaStream_t s) {
+  if (g.n_a <= 0) return 0;
+  const int64_t n = (int64_t)g.nnz > (int64_t)g.n_a ? (int64_t)g.nnz : (int64_t)g.n_a;
+  const int64_t cap = (int64_t)sms * 8;
+  const int64_t grid = div_up(n, (int64_t)kNT) < cap ? div_up(n, (int64_t)kNT) : cap;
+  k_net_publish<<<(int)grid, kNT, 0, s>>>(g.b_idx, g.nnz, netc, rank, g.n_a, nc, colors, lose);
   return 1;
 }
 

@@ -143,3 +143,57 @@ def test_rmat22_d2gc_sampled(bg, ctx, rmat22, policy):
     colors, st, rc = run(policy=policy)
     assert rc == bg.BGPC_OK
     assert per_net_valid(cn.b_ptr, cn.b_idx, cn.n_b, colors.cpu().numpy())
+
+
+def test_chung_lu_4m_net_round(bg, ctx):
+    """N1 on the full-size power-law graph: the whole net round (tentative
+    colors before removal, and the work queue after it) equals the oracle's,
+    which is linear in nnz; the vertex-based waves after it are sampled."""
+    g = gg.chung_lu(1 << 22, 16.0, 50000.0, 2.1, seed=2)
+    dg = bg.DeviceGraph.from_host(g, "cuda:0")
+    run = lambda **kw: bg.bgpc_color(ctx, dg, net_rounds=1, **kw)
+    ref = O.rs_color(g, net_rounds=1, stop_after_waves=1, stop_before_removal=True)
+    got, st, rc = run(stop_after_waves=1, stop_before_removal=True)
+    assert rc == bg.BGPC_STOPPED and np.array_equal(got.cpu().numpy(), ref.colors)
+    rng = np.random.default_rng(17)
+    # the round-2 work queue holds exactly the net round's losers (the
+    # conflict rule on sampled vertices; every vertex is in W_1, id order)
+    W_out = torch.empty(g.n_a, dtype=torch.int32, device="cuda:0")
+    _, st2, rc = run(stop_after_waves=1, W_out=W_out)  # start of round 2, wave 0
+    assert rc == bg.BGPC_STOPPED and st2["stopped_wave"] == 0 and st2["rounds"] == 2
+    inW2 = np.zeros(g.n_a, bool)
+    inW2[W_out[:st2["stopped_m"]].cpu().numpy()] = True
+    which = rng.choice(g.n_a, size=400, replace=False).astype(np.int32)
+    lose, status = O.rs_losers(g, ref.colors, np.arange(g.n_a, dtype=np.int32), which)
+    assert status == O.OK and np.array_equal(lose.astype(bool), inW2[which])
+    n = sampled_wave_parity_n1(bg, g, run, rng)
+    assert n > 500
+    colors, st, rc = run()
+    assert rc == bg.BGPC_OK
+    assert per_net_valid(g.b_ptr, g.b_idx, g.n_b, colors.cpu().numpy())
+
+
+def sampled_wave_parity_n1(bg, g, run, rng, per_wave=12, budget=3e8):
+    """Waves of the vertex-based rounds after the net round (wave counts
+    shifted by the net round's one wave)."""
+    W_out = torch.empty(g.n_a, dtype=torch.int32, device="cuda:0")
+    checked = 0
+    for s in (2, 9, 17):
+        col_s, st_s, rc = run(stop_after_waves=s, W_out=W_out)
+        assert rc == bg.BGPC_STOPPED
+        q, m = st_s["stopped_wave"], st_s["stopped_m"]
+        S = col_s.cpu().numpy()
+        W = W_out[:m].cpu().numpy()
+        col_n, _, rc = run(stop_after_waves=s + 1, stop_before_removal=True)
+        nxt = col_n.cpu().numpy()
+        nch = (m + C - 1) // C
+        chunks = np.array([j for j in range(nch) if rs_py.wave_of(j, Q) == q], np.int64)
+        vol = chunk_volume(g, W, m)[chunks]
+        cheap = chunks[vol <= budget]
+        pick = rng.choice(cheap, size=min(per_wave, len(cheap)), replace=False)
+        out = O.rs_chunks(g, S, W, pick.astype(np.int32), O.FF, chunk=C, big_net=T, nthreads=16)
+        for j in pick:
+            pos = np.arange(j * C, min(m, (j + 1) * C))
+            assert np.array_equal(out[pos], nxt[W[pos]]), f"wave start {s}, chunk {j}"
+            checked += len(pos)
+    return checked

@@ -36,12 +36,14 @@ def run_gpu(bg, ctx, g, **kw):
     return colors.cpu().numpy(), st, rc, dg
 
 
-def assert_parity(bg, ctx, g, policy=O.FF, chunk=64, waves=16, big_net=64, rank=None, **kw):
+def assert_parity(bg, ctx, g, policy=O.FF, chunk=64, waves=16, big_net=64, rank=None,
+                  net_rounds=0, **kw):
     ref = O.rs_color(g, policy, chunk=chunk, waves=waves, big_net=big_net, rank=rank,
-                     nthreads=8)
+                     nthreads=8, net_rounds=net_rounds)
     assert ref.status == O.OK
     got, st, rc, dg = run_gpu(bg, ctx, g, policy=policy, chunk=chunk, waves=waves,
-                              big_net=big_net, rank=rank, validate=True, **kw)
+                              big_net=big_net, rank=rank, validate=True,
+                              net_rounds=net_rounds, **kw)
     assert rc == bg.BGPC_OK
     bad = np.nonzero(got != ref.colors)[0]
     assert bad.size == 0, f"{bad.size} colors differ, first at {bad[:8]}"
@@ -337,3 +339,66 @@ def test_wave_snapshots_match(bg, ctx):
         assert st["stopped_m"] == ref.m and st["stopped_wave"] == ref.wave
         assert np.array_equal(colors.cpu().numpy(), ref.colors)
         assert np.array_equal(W_out[:ref.m].cpu().numpy(), ref.W)
+
+
+# ------------------------------------------------- net-based first round (N1)
+
+@pytest.mark.parametrize("policy", POLICIES)
+def test_net_round_parity(bg, ctx, policy):
+    """N1-*: the first round colored net by net (Alg. 8), the later rounds by
+    vertex waves; colors, rounds, |W_r| and traversal equal the oracle's."""
+    rng = np.random.default_rng(71)
+    graphs = [gg.random_bipartite(2000, 2000, 5, seed=1), gg.stencil9(64),
+              gg.chung_lu(20000, 16, 1500, 2.1, seed=4), hub_graph(),
+              gg.from_nets(7, [[0, 1, 2], [], [2, 4], [5]]),      # isolated vertices 3 and 6
+              gg.from_nets(40, [list(range(40))])]
+    for g in graphs:
+        assert_parity(bg, ctx, g, policy=policy, net_rounds=1)
+    g = gg.chung_lu(20000, 16, 1500, 2.1, seed=4)
+    rank = rng.permutation(g.n_a).astype(np.int32)
+    assert_parity(bg, ctx, g, policy=policy, net_rounds=1, rank=rank)
+    assert_parity(bg, ctx, g, policy=policy, net_rounds=1, chunk=7, waves=5, big_net=20)
+    for d in (1, 2):
+        assert_parity(bg, ctx, hub_graph(), policy=policy, net_rounds=1, detect=d)
+
+
+def test_net_round_tentative_colors(bg, ctx):
+    """Stopped before its conflict removal, the net round's tentative colors
+    and work queue equal the oracle's (a net round counts as one wave)."""
+    for g in (gg.chung_lu(20000, 16, 1500, 2.1, seed=4), gg.stencil9(50)):
+        ref = O.rs_color(g, net_rounds=1, stop_after_waves=1, stop_before_removal=True)
+        assert ref.status == O.STOPPED and ref.wave == 1
+        W = torch.empty(g.n_a, dtype=torch.int32, device="cuda:0")
+        got, st, rc, _ = run_gpu(bg, ctx, g, net_rounds=1, stop_after_waves=1,
+                                 stop_before_removal=True, W_out=W)
+        assert rc == bg.BGPC_STOPPED and st["stopped_wave"] == 1
+        assert np.array_equal(got, ref.colors)
+        assert np.array_equal(W[:st["stopped_m"]].cpu().numpy(), ref.W)
+        # one wave later: the first vertex-based wave of round 2
+        ref2 = O.rs_color(g, net_rounds=1, stop_after_waves=2)
+        got2, st2, rc2, _ = run_gpu(bg, ctx, g, net_rounds=1, stop_after_waves=2)
+        assert rc2 == bg.BGPC_STOPPED and np.array_equal(got2, ref2.colors)
+
+
+@pytest.mark.parametrize("policy", [O.FF, O.B1, O.B2])
+def test_net_round_d2gc(bg, ctx, policy):
+    """D2GC with the net-based first round in Alg. 9's order (the center of
+    N[v] first)."""
+    for ug in (gg.rmat(12, 16, seed=3), gg.from_edges(4, [(2, 0), (2, 1), (2, 3)])):
+        cn = O.closed_nbhd(ug)
+        ref = O.rs_color(cn, policy, net_rounds=1, center_first=True, nthreads=8)
+        dug = bg.DeviceUGraph.from_host(ug, "cuda:0")
+        got, st, rc = bg.d2gc_color(ctx, dug, policy=policy, net_rounds=1)
+        assert rc == bg.BGPC_OK
+        assert np.array_equal(got.cpu().numpy(), ref.colors)
+        assert st["rounds"] == ref.rounds and st["w_per_round"] == ref.w_per_round.tolist()
+        assert O.d2_conflicts(ug, got.cpu().numpy()) == 0
+
+
+def test_net_rounds_limit(bg, ctx):
+    """Only the first round can be net-based on the GPU (N1-*)."""
+    dg = bg.DeviceGraph.from_host(gg.random_bipartite(300, 200, 4, seed=2), "cuda:0")
+    for nr in (-1, 2):
+        with pytest.raises(bg.BgpcError) as e:
+            bg.bgpc_color(ctx, dg, net_rounds=nr)
+        assert e.value.status == bg.BGPC_EINVAL
