@@ -508,9 +508,12 @@ def run_gpu(args):
 
     batched = args.workload == "batch512"
 
+    last_rounds = []
+
     def step(profile=False):
         if batched:
-            _, st, _, _ = bg.bgpc_color_batched(ctx, dgs, colors, profile=profile)
+            _, st, rounds, _ = bg.bgpc_color_batched(ctx, dgs, colors, profile=profile)
+            last_rounds[:] = rounds
             return [st]
         sts = []
         for dg, c in zip(dgs, colors):
@@ -573,6 +576,16 @@ def run_gpu(args):
                          + 28 * (tot("w_total") - tot("w_large")),
                          tot("trav_total") - tot("trav_large")),
     }
+    if batched:
+        # the persistent kernel: 8 B per traversed two-hop entry (the member id
+        # and its color), 12 B per incidence (a_idx and the b_ptr pair), 28 B
+        # per work-queue entry (queue, a_ptr pair, sums, stage, colors) and,
+        # per round, 8 B per CSC entry for the per-net conflict detection
+        det = sum(g.nnz * r for g, r in zip(graphs, last_rounds))
+        kern = {"k_batch": (tot("ms_color"), 8 * tot("trav_total") + 12 * tot("incid_total")
+                            + 28 * tot("w_total") + 8 * det * args.steps,
+                            tot("trav_total"))}
+        n_launch = args.steps
     dom = max(kern, key=lambda k: kern[k][0])
     dom_ms, dom_bytes, dom_entries = kern[dom]
     peak, peak_kind = peaks()

@@ -122,8 +122,20 @@ typedef struct {
                                 the setup and after every round); when exceeded the
                                 call returns BGPC_ETIMEOUT (outputs undefined).
                                 0 = no limit */
-    int32_t reserved[4];
+    int32_t batch_engine;    /* bgpc_color_batched only, a mapping parameter (results do
+                                not change): BGPC_BATCH_PERSISTENT (0, default: one
+                                persistent launch with a device task queue, captured
+                                in a CUDA graph) or BGPC_BATCH_STREAMS (1: the
+                                single-graph engine on batch_streams host workers) */
+    int32_t batch_mapping;   /* BGPC_BATCH_PERSISTENT: 0 = the mapping the autotuner
+                                measured fastest for this batch (tuned on the first
+                                call, then cached in the context); k in
+                                [1, BGPC_BATCH_MAPPINGS] = candidate k - 1 */
+    int32_t reserved[2];
 } bgpc_opts_t;
+
+enum { BGPC_BATCH_PERSISTENT = 0, BGPC_BATCH_STREAMS = 1 };
+#define BGPC_BATCH_MAPPINGS 12   /* autotuner candidates of the persistent engine */
 
 enum { BGPC_DETECT_AUTO = 0, BGPC_DETECT_NETS = 1, BGPC_DETECT_PAIRS = 2 };
 enum { BGPC_GATHER_AUTO = 0, BGPC_GATHER_CTA = 1 };
@@ -184,15 +196,21 @@ int bgpc_color(bgpc_ctx_t *ctx, const bgpc_graph_t *g, const bgpc_opts_t *opts,
 /* Batched BGPC: colors n_graphs independent bipartite graphs with one call
  * (no counterpart in the paper, which colors one graph at a time).  Every
  * graph gets exactly the coloring that bgpc_color gives it with the same
- * opts: the graphs are colored one after the other by the single-graph
- * engine, sharing the context's scratch.  graphs: host array [n_graphs] of
- * graphs with device arrays; colors: host array [n_graphs] of device int32
- * pointers ([n_a] each).  stats (host, may be NULL): the whole batch
- * (rounds and colors = the largest over the graphs; the per-round and total
- * counters and phase times summed).  rounds_out / ncolors_out: host
- * [n_graphs] or NULL, per graph.  opts.rank must be NULL and
- * opts.stop_after_waves 0 (else BGPC_EINVAL); n_graphs in [1, 65535].
- * Synchronises `stream`. */
+ * opts (id order).  By default (opts.batch_engine = BGPC_BATCH_PERSISTENT)
+ * one persistent kernel colors all graphs: per graph a device ticket hands
+ * out the tasks of its current phase (waves, publication, detection,
+ * compaction) to whichever CTA is free, and the launch sequence is captured
+ * in a CUDA graph that later calls on the same batch replay; a graph whose
+ * colors outgrow the engine's shared-memory window is then colored by the
+ * single-graph engine.  graphs: host array [n_graphs] of graphs with device
+ * arrays; colors: host array [n_graphs] of device int32 pointers ([n_a]
+ * each).  stats (host, may be NULL): the whole batch (rounds and colors =
+ * the largest over the graphs; the per-round and total counters summed).
+ * rounds_out / ncolors_out: host [n_graphs] or NULL, per graph.  opts.rank
+ * must be NULL, opts.stop_after_waves and opts.net_rounds 0 (else
+ * BGPC_EINVAL); n_graphs in [1, 65535].  BGPC_ETIMEOUT if the persistent
+ * launch made no progress for opts.timeout_us (default 10 s).  Synchronises
+ * `stream`. */
 int bgpc_color_batched(bgpc_ctx_t *ctx, int32_t n_graphs, const bgpc_graph_t *graphs,
                        const bgpc_opts_t *opts, int32_t *const *colors, bgpc_stats_t *stats,
                        int32_t *rounds_out, int32_t *ncolors_out, void *stream);

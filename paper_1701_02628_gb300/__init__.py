@@ -25,6 +25,8 @@ BGPC_ETIMEOUT, BGPC_EUNSORTED, BGPC_EINTERNAL = -5, -6, -7
 BGPC_FF, BGPC_B1, BGPC_B2, BGPC_B2X = 0, 1, 2, 3
 BGPC_DETECT_AUTO, BGPC_DETECT_NETS, BGPC_DETECT_PAIRS = 0, 1, 2
 BGPC_GATHER_AUTO, BGPC_GATHER_CTA = 0, 1
+BGPC_BATCH_PERSISTENT, BGPC_BATCH_STREAMS = 0, 1
+BGPC_BATCH_MAPPINGS = 12
 BGPC_MAX_REPORT = 64
 NO_BIG = (1 << 31) - 1
 
@@ -51,7 +53,8 @@ class bgpc_opts_t(ctypes.Structure):
                 ("profile", ctypes.c_int32), ("stop_before_removal", ctypes.c_int32),
                 ("batch_streams", ctypes.c_int32), ("detect", ctypes.c_int32),
                 ("gather", ctypes.c_int32), ("net_rounds", ctypes.c_int32),
-                ("timeout_us", ctypes.c_int64), ("reserved", ctypes.c_int32 * 4)]
+                ("timeout_us", ctypes.c_int64), ("batch_engine", ctypes.c_int32),
+                ("batch_mapping", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
 
 
 class bgpc_stats_t(ctypes.Structure):
@@ -262,7 +265,7 @@ def make_opts(policy=BGPC_FF, chunk=64, waves=16, big_net=64, rank=None, max_rou
               validate=False, stop_after_waves=0, W_out=None, want_balance=False,
               profile=False, stop_before_removal=False, batch_streams=0,
               detect=BGPC_DETECT_AUTO, gather=BGPC_GATHER_AUTO, net_rounds=0,
-              timeout_us=0) -> bgpc_opts_t:
+              timeout_us=0, batch_engine=0, batch_mapping=0) -> bgpc_opts_t:
     o = bgpc_opts_default()
     o.policy, o.chunk, o.waves, o.big_net = policy, chunk, waves, big_net
     o.rank = _ptr(rank)
@@ -278,6 +281,8 @@ def make_opts(policy=BGPC_FF, chunk=64, waves=16, big_net=64, rank=None, max_rou
     o.gather = gather
     o.net_rounds = net_rounds
     o.timeout_us = timeout_us
+    o.batch_engine = batch_engine
+    o.batch_mapping = batch_mapping
     return o
 
 

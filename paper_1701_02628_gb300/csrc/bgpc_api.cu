@@ -510,6 +510,315 @@ int color_impl(bgpc_ctx_t *ctx, const bgpc_graph_t &g, const bgpc_opts_t &o, int
   return BGPC_OK;
 }
 
+
+// ------------------------------------------------ batched, persistent engine
+
+// Mapping candidates of the persistent engine: forbidden-window words per
+// vertex, CTAs per SM (0 = as many as fit), chunk indices per wave task
+// (times Q), vertices / positions / nets per task, and the largest round (in
+// chunks) that one CTA runs as a single task.  None changes a result.
+const BatchMapping kBatchMaps[BGPC_BATCH_MAPPINGS] = {
+    {32, 0, 1, 2048, 32}, {32, 0, 4, 2048, 32}, {16, 0, 1, 2048, 32}, {16, 0, 4, 2048, 32},
+    {64, 0, 1, 2048, 32}, {64, 0, 4, 2048, 32}, {32, 0, 1, 2048, 0},  {32, 0, 1, 2048, 128},
+    {16, 0, 1, 2048, 128}, {32, 4, 1, 2048, 32}, {64, 4, 4, 2048, 0},  {16, 4, 4, 2048, 128}};
+
+unsigned long long fnv(unsigned long long h, const void *p, size_t n) {
+  const unsigned char *b = static_cast<const unsigned char *>(p);
+  for (size_t i = 0; i < n; i++) {
+    h ^= b[i];
+    h *= 1099511628211ull;
+  }
+  return h;
+}
+
+// Identity of a batch: its graphs (pointers and sizes), outputs and the
+// semantic options.  Equal keys color the same arrays the same way.
+unsigned long long batch_key(int32_t G, const bgpc_graph_t *graphs, int32_t *const *colors,
+                             const bgpc_opts_t &o) {
+  unsigned long long h = 1469598103934665603ull;
+  h = fnv(h, &G, sizeof(G));
+  h = fnv(h, graphs, sizeof(bgpc_graph_t) * (size_t)G);
+  h = fnv(h, colors, sizeof(int32_t *) * (size_t)G);
+  const int32_t sem[5] = {o.policy, o.chunk, o.waves, o.big_net, o.max_rounds};
+  return fnv(h, sem, sizeof(sem));
+}
+
+struct BatchHost {  // views into the pinned staging block
+  BatchDesc *desc;
+  BatchState *st;
+  BatchGlobal *glob;
+  BatchStat *stat;
+};
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+int batch_host_views(bgpc_ctx_t *ctx, int32_t G, BatchHost *h) {
+  const size_t o1 = align_up(sizeof(BatchDesc) * (size_t)G, 128);
+  const size_t o2 = o1 + align_up(sizeof(BatchState) * (size_t)G, 128);
+  const size_t o3 = o2 + align_up(sizeof(BatchGlobal), 128);
+  const size_t need = o3 + sizeof(BatchStat) * (size_t)G;
+  if (need > ctx->h_batch_cap) {
+    if (ctx->h_batch) cudaFreeHost(ctx->h_batch);
+    ctx->h_batch = nullptr;
+    ctx->h_batch_cap = 0;
+    if (ctx->bexec) {  // the captured launch copies from the old block
+      cudaGraphExecDestroy(ctx->bexec);
+      ctx->bexec = nullptr;
+    }
+    CU(cudaMallocHost(&ctx->h_batch, need));
+    ctx->h_batch_cap = need;
+  }
+  char *b = static_cast<char *>(ctx->h_batch);
+  h->desc = reinterpret_cast<BatchDesc *>(b);
+  h->st = reinterpret_cast<BatchState *>(b + o1);
+  h->glob = reinterpret_cast<BatchGlobal *>(b + o2);
+  h->stat = reinterpret_cast<BatchStat *>(b + o3);
+  return BGPC_OK;
+}
+
+// One run of the persistent engine with mapping `map` on ctx->bstream
+// (ordered after everything already on `s`, and `s` after it).  With
+// use_graph, the launch sequence is captured in a CUDA graph, cached in the
+// context with the batch key and replayed by later calls on the same batch.
+// Per-graph results land in the pinned statistics (h->stat).
+int batch_once(bgpc_ctx_t *ctx, int32_t G, const bgpc_graph_t *graphs, int32_t *const *colors,
+               const bgpc_opts_t &o, const BatchMapping &map, int map_id, cudaStream_t s,
+               bool use_graph, BatchHost *h, float *ms_kernel) {
+  int64_t voff = 0, noff = 0, toff = 0;
+  int32_t empty = 0;
+  const int32_t tile = map.tile;
+  for (int32_t k = 0; k < G; k++) {
+    const bgpc_graph_t &gk = graphs[k];
+    BatchDesc &d = h->desc[k];
+    d.a_ptr = gk.a_ptr;
+    d.a_idx = gk.a_idx;
+    d.b_ptr = gk.b_ptr;
+    d.b_idx = gk.b_idx;
+    d.colors = colors[k];
+    d.n_a = gk.n_a;
+    d.n_b = gk.n_b;
+    d.nnz = gk.nnz;
+    d.pad = 0;
+    d.voff = voff;
+    d.noff = noff;
+    d.toff = toff;
+    voff += gk.n_a;
+    noff += gk.n_b;
+    toff += (gk.n_a + tile - 1) / tile + 1;
+    BatchState &st = h->st[k];
+    memset(&st, 0, sizeof(st));
+    const int32_t nt = gk.n_a > 0 ? (gk.n_a + tile - 1) / tile + (gk.n_b + tile - 1) / tile : 0;
+    st.ticket = (unsigned long long)(uint32_t)nt << 24;
+    st.ntasks = nt;
+    st.phase = 0;  // analysis
+    st.gmax_fixed = -1;
+    st.status = gk.n_a > 0 ? kBatchRunning : kBatchDone;
+    empty += gk.n_a > 0 ? 0 : 1;
+  }
+  memset(h->glob, 0, sizeof(BatchGlobal));
+  h->glob->finished = empty;
+  const size_t nv = (size_t)(voff > 0 ? voff : 1), nn = (size_t)(noff > 0 ? noff : 1);
+  CU(grow(ctx->bW0, nv));
+  CU(grow(ctx->bW1, nv));
+  CU(grow(ctx->bstage, nv));
+  CU(grow(ctx->bown, nv));
+  CU(grow(ctx->bsown, nv));
+  CU(grow(ctx->bd2, nv));
+  CU(grow(ctx->bkofs, nv));
+  CU(grow(ctx->blose, nv));
+  CU(grow(ctx->binW, nv));
+  CU(grow(ctx->bbig, nn));
+  CU(grow(ctx->bntag, nn));
+  CU(grow(ctx->btcnt, (size_t)toff + 1));
+  CU(grow(ctx->btofs, (size_t)toff + 1));
+  CU(grow(ctx->bdesc, (size_t)G));
+  CU(grow(ctx->bst, (size_t)G));
+  CU(grow(ctx->bstat, (size_t)G));
+  CU(grow(ctx->bglob, 1));
+  if (!ctx->bstream) CU(cudaStreamCreateWithFlags(&ctx->bstream, cudaStreamNonBlocking));
+  for (int i = 0; i < 4; i++)
+    if (!ctx->bev[i]) CU(cudaEventCreate(&ctx->bev[i]));
+  cudaStream_t bs = ctx->bstream;
+  CU(cudaEventRecord(ctx->bev[0], s));
+  CU(cudaStreamWaitEvent(bs, ctx->bev[0], 0));
+
+  BatchLaunch L;
+  L.desc = ctx->bdesc.p;
+  L.st = ctx->bst.p;
+  L.stat = ctx->bstat.p;
+  L.glob = ctx->bglob.p;
+  L.G = G;
+  L.C = o.chunk;
+  L.Q = o.waves;
+  L.T = o.big_net;
+  L.max_rounds = o.max_rounds;
+  L.policy = o.policy;
+  L.sms = ctx->num_sms;
+  L.timeout_ns = o.timeout_us > 0 ? o.timeout_us * 1000 : 10000000000ll;
+  L.map = map;
+  L.W0 = ctx->bW0.p;
+  L.W1 = ctx->bW1.p;
+  L.stage = ctx->bstage.p;
+  L.own = ctx->bown.p;
+  L.s_own = ctx->bsown.p;
+  L.d2 = ctx->bd2.p;
+  L.kofs = ctx->bkofs.p;
+  L.big = ctx->bbig.p;
+  L.tcnt = ctx->btcnt.p;
+  L.tofs = ctx->btofs.p;
+  L.ntag = ctx->bntag.p;
+  L.lose = ctx->blose.p;
+  L.inW = ctx->binW.p;
+
+  auto enqueue = [&](cudaStream_t st) -> int {
+    CU(cudaMemcpyAsync(ctx->bdesc.p, h->desc, sizeof(BatchDesc) * (size_t)G,
+                       cudaMemcpyHostToDevice, st));
+    CU(cudaMemcpyAsync(ctx->bst.p, h->st, sizeof(BatchState) * (size_t)G, cudaMemcpyHostToDevice,
+                       st));
+    CU(cudaMemcpyAsync(ctx->bglob.p, h->glob, sizeof(BatchGlobal), cudaMemcpyHostToDevice, st));
+    CU(cudaMemsetAsync(ctx->bstat.p, 0, sizeof(BatchStat) * (size_t)G, st));
+    CU(launch_batch(L, st));
+    CU(cudaMemcpyAsync(h->stat, ctx->bstat.p, sizeof(BatchStat) * (size_t)G,
+                       cudaMemcpyDeviceToHost, st));
+    CU(cudaMemcpyAsync(h->glob, ctx->bglob.p, sizeof(BatchGlobal), cudaMemcpyDeviceToHost, st));
+    return BGPC_OK;
+  };
+  int rc;
+  unsigned long long key = batch_key(G, graphs, colors, o);
+  key = fnv(key, &map_id, sizeof(map_id));
+  // the launch sequence (descriptor uploads, the persistent kernel, the
+  // statistics download) is timed from outside any capture
+  CU(cudaEventRecord(ctx->bev[2], bs));
+  if (use_graph && ctx->bexec && ctx->bkey == key) {
+    CU(cudaGraphLaunch(ctx->bexec, bs));
+  } else if (use_graph &&
+             cudaStreamBeginCapture(bs, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+    rc = enqueue(bs);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(bs, &graph);
+    if (rc != BGPC_OK || ec != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      cudaGetLastError();
+      return rc != BGPC_OK ? rc : BGPC_ECUDA;
+    }
+    if (ctx->bexec) cudaGraphExecDestroy(ctx->bexec);
+    ctx->bexec = nullptr;
+    const cudaError_t ei = cudaGraphInstantiate(&ctx->bexec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ei != cudaSuccess) {
+      cudaGetLastError();
+      ctx->bexec = nullptr;
+      return BGPC_ECUDA;
+    }
+    ctx->bkey = key;
+    CU(cudaGraphLaunch(ctx->bexec, bs));
+  } else {
+    cudaGetLastError();
+    if ((rc = enqueue(bs))) return rc;
+  }
+  CU(cudaEventRecord(ctx->bev[3], bs));
+  CU(cudaEventRecord(ctx->bev[1], bs));
+  CU(cudaStreamWaitEvent(s, ctx->bev[1], 0));
+  CU(cudaStreamSynchronize(bs));
+  if (ms_kernel) {
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, ctx->bev[2], ctx->bev[3]) != cudaSuccess) {
+      cudaGetLastError();
+      t = 0.f;
+    }
+    *ms_kernel = t;
+  }
+  if (h->glob->err) return BGPC_ETIMEOUT;
+  return BGPC_OK;
+}
+
+int batch_persistent(bgpc_ctx_t *ctx, int32_t G, const bgpc_graph_t *graphs,
+                     int32_t *const *colors, const bgpc_opts_t &o, bgpc_stats_t *stats,
+                     int32_t *rounds_out, int32_t *ncolors_out, cudaStream_t s,
+                     const Deadline &dl) {
+  BatchHost h;
+  int rc = batch_host_views(ctx, G, &h);
+  if (rc) return rc;
+  int map_id = o.batch_mapping > 0 ? o.batch_mapping - 1 : -1;
+  const unsigned long long key = batch_key(G, graphs, colors, o);
+  if (map_id < 0) {
+    for (const auto &e : ctx->btuned)
+      if (e.first == key) map_id = e.second;
+  }
+  if (map_id < 0) {
+    // autotune: one timed run of every candidate on this batch; the fastest
+    // is kept for later calls on it (the results are the same for all)
+    float best = -1.f;
+    for (int c = 0; c < BGPC_BATCH_MAPPINGS; c++) {
+      float ms = 0.f;
+      if ((rc = batch_once(ctx, G, graphs, colors, o, kBatchMaps[c], c, s, false, &h, &ms)))
+        return rc;
+      int32_t nfall = 0;
+      for (int32_t k = 0; k < G; k++) nfall += h.stat[k].status == kBatchWindow;
+      ms += 1000.f * (float)nfall;  // graphs handed back cost a single-graph coloring each
+      if (best < 0.f || ms < best) {
+        best = ms;
+        map_id = c;
+      }
+    }
+    if (ctx->btuned.size() > 64) ctx->btuned.erase(ctx->btuned.begin());
+    ctx->btuned.emplace_back(key, map_id);
+  }
+  float ms_k = 0.f;
+  if ((rc = batch_once(ctx, G, graphs, colors, o, kBatchMaps[map_id], map_id, s, true, &h,
+                       &ms_k)))
+    return rc;
+  // per-graph outcome: done, or handed to the single-graph engine
+  bgpc_stats_t tot;
+  memset(&tot, 0, sizeof(tot));
+  tot.kernel_launches = 1;
+  tot.color_launches = 1;
+  tot.ms_color = o.profile ? ms_k : 0.0;
+  for (int32_t k = 0; k < G; k++) {
+    const BatchStat &x = h.stat[k];
+    const int32_t status = graphs[k].n_a > 0 ? x.status : kBatchDone;
+    int32_t rounds = x.rounds, ncol = x.colors;
+    if (status == kBatchRounds) return BGPC_EROUNDS;
+    if (status == kBatchWindow) {
+      bgpc_stats_t one;
+      memset(&one, 0, sizeof(one));
+      if ((rc = color_impl(ctx, graphs[k], o, colors[k], &one, s, dl))) return rc;
+      rounds = one.rounds;
+      ncol = one.colors;
+      for (int r = 0; r < BGPC_MAX_REPORT && r < one.rounds; r++) {
+        tot.w_per_round[r] += one.w_per_round[r];
+        tot.trav_per_round[r] += one.trav_per_round[r];
+      }
+      tot.trav_total += one.trav_total;
+      tot.incid_total += one.incid_total;
+      tot.w_total += one.w_total;
+      tot.kernel_launches += one.kernel_launches;
+      tot.pieces_total++;  // graphs handed to the single-graph engine
+    } else if (status != kBatchDone) {
+      return BGPC_EINTERNAL;
+    } else {
+      for (int r = 0; r < BGPC_MAX_REPORT && r < kBatchReport && r < x.rounds; r++) {
+        tot.w_per_round[r] += x.w_per_round[r];
+        tot.trav_per_round[r] += x.trav_per_round[r];
+      }
+      tot.trav_total += x.trav_total;
+      tot.incid_total += x.incid_total;
+      tot.w_total += x.w_total;
+    }
+    if (graphs[k].n_a == 0) {
+      rounds = 0;
+      ncol = 0;
+    }
+    if (rounds_out) rounds_out[k] = rounds;
+    if (ncolors_out) ncolors_out[k] = ncol;
+    tot.rounds = rounds > tot.rounds ? rounds : tot.rounds;
+    tot.colors = ncol > tot.colors ? ncol : tot.colors;
+  }
+  tot.ms_total = dl.ms();
+  if (stats) *stats = tot;
+  return BGPC_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -575,6 +884,16 @@ int bgpc_ctx_destroy(bgpc_ctx_t *ctx) {
   ctx->subs.clear();
   ctx->sub_streams.clear();
   release(ctx->card); release(ctx->bad);
+  release(ctx->bW0); release(ctx->bW1); release(ctx->bstage); release(ctx->bown);
+  release(ctx->bsown); release(ctx->bd2); release(ctx->bkofs); release(ctx->bbig);
+  release(ctx->btcnt); release(ctx->btofs); release(ctx->blose); release(ctx->binW);
+  release(ctx->bntag);
+  release(ctx->bdesc); release(ctx->bst); release(ctx->bstat); release(ctx->bglob);
+  if (ctx->bexec) cudaGraphExecDestroy(ctx->bexec);
+  if (ctx->h_batch) cudaFreeHost(ctx->h_batch);
+  if (ctx->bstream) cudaStreamDestroy(ctx->bstream);
+  for (cudaEvent_t e : ctx->bev)
+    if (e) cudaEventDestroy(e);
   release(ctx->rkey0); release(ctx->rkey1); release(ctx->rval0); release(ctx->rval1);
   release(ctx->rhist); release(ctx->rsum); release(ctx->mpart); release(ctx->mgrad);
   for (cudaEvent_t e : ctx->events) cudaEventDestroy(e);
@@ -610,9 +929,36 @@ int bgpc_color_batched(bgpc_ctx_t *ctx, int32_t n_graphs, const bgpc_graph_t *gr
     if ((rc = check_graph_args(&graphs[k]))) return rc;
     if (graphs[k].n_a > 0 && !colors[k]) return BGPC_EINVAL;
   }
+  if (opts->net_rounds != 0 || opts->batch_engine < BGPC_BATCH_PERSISTENT ||
+      opts->batch_engine > BGPC_BATCH_STREAMS || opts->batch_mapping < 0 ||
+      opts->batch_mapping > BGPC_BATCH_MAPPINGS)
+    return BGPC_EINVAL;
   Guard guard(ctx->device);
   Deadline dl(opts->timeout_us);
   cudaStream_t s = (cudaStream_t)stream;
+  if (opts->validate) {
+    for (int32_t k = 0; k < n_graphs; k++) {
+      const bgpc_graph_t &gk = graphs[k];
+      if (gk.n_a > 0 && (rc = validate_csr(ctx, gk.a_ptr, gk.a_idx, gk.n_a, gk.nnz, gk.n_b, s)))
+        return rc;
+      if (gk.n_b > 0 && (rc = validate_csr(ctx, gk.b_ptr, gk.b_idx, gk.n_b, gk.nnz, gk.n_a, s)))
+        return rc;
+    }
+  }
+  // the persistent engine's task counters hold up to 2^23 tasks per phase
+  bool fits = true;
+  for (int32_t k = 0; k < n_graphs; k++) {
+    const int64_t na = graphs[k].n_a, nb = graphs[k].n_b;
+    const int64_t nch = (na + opts->chunk - 1) / opts->chunk;
+    if ((na + 1023) / 1024 + (nb + 1023) / 1024 >= (1 << 23) || nch / opts->waves >= (1 << 23))
+      fits = false;
+  }
+  if (opts->batch_engine == BGPC_BATCH_PERSISTENT && fits) {
+    bgpc_opts_t o = *opts;
+    o.validate = 0;
+    return batch_persistent(ctx, n_graphs, graphs, colors, o, stats, rounds_out, ncolors_out, s,
+                            dl);
+  }
   int K = opts->batch_streams > 0 ? opts->batch_streams : 8;
   if (K > n_graphs) K = n_graphs;
   while ((int)ctx->subs.size() < K) {

@@ -79,6 +79,58 @@ struct Buf {
   size_t cap = 0;
 };
 
+// Batched coloring in one persistent launch (bgpc_batch.cu).
+constexpr int kBatchReport = 64;  // rounds reported per graph
+enum : int32_t {
+  kBatchRunning = 0,
+  kBatchDone = 1,
+  kBatchWindow = 2,   // colors outgrew the shared-memory window: single-graph engine
+  kBatchRounds = 3,   // more than max_rounds rounds
+  kBatchFailed = 4,   // internal error
+};
+struct BatchDesc {    // one graph of the batch (read-only during the launch)
+  const int32_t *a_ptr, *a_idx, *b_ptr, *b_idx;
+  int32_t *colors;
+  int32_t n_a, n_b, nnz, pad;
+  int64_t voff;       // offset of the graph's vertex scratch (n_a entries per pool)
+  int64_t noff;       // offset of its net scratch (n_b entries)
+  int64_t toff;       // offset of its tile scratch (tiles of W + 1)
+};
+struct __align__(128) BatchState {  // one graph's progress (zeroed but for the ticket)
+  unsigned long long ticket;  // sequence:16 | tasks of the phase:24 | next task:24
+  int32_t done;               // finished tasks of the current phase
+  int32_t ntasks;
+  int32_t seq;
+  int32_t phase, q, r, m, nch, cur;
+  int32_t col_max0;           // chunk-private col_max at the start of a wave: max color published
+  int32_t gmax_fixed;         // largest color of the vertices outside W_r
+  int32_t gmax_wave;          // largest color published in this round so far
+  int32_t gmax_win;           // largest color kept by this round's winners
+  int32_t m_next, ntiles, nbig, status;
+  int32_t tagged;             // this round's detection visits only nets tagged r + 1
+  int32_t tag_next;           // the scatter tags the nets of W_{r+1} with r + 2
+};
+struct BatchStat {    // one graph's statistics (zeroed before the launch)
+  int32_t rounds, colors, status, pad;
+  int64_t w_per_round[kBatchReport];
+  int64_t trav_per_round[kBatchReport];
+  int64_t trav_total, w_total, incid_total;
+};
+constexpr int kBatchPosts = 1024;  // ring of recently posted graphs (a power of two)
+struct BatchGlobal {
+  int32_t finished;              // graphs done (or handed back)
+  int32_t err;                   // 1: a CTA saw no progress for timeout_ns
+  unsigned long long progress;   // phase advances so far
+  uint32_t posts;                // phases posted so far ...
+  int32_t post[kBatchPosts];     // ... and the graph of each, by post count mod the ring
+};
+struct BatchMapping {  // mapping parameters: they never change a result
+  int32_t ww;          // forbidden-window words per vertex: 16, 32 or 64
+  int32_t ctas_per_sm; // 0 = as many as fit
+  int32_t cpt;         // a wave task covers cpt * Q chunk indices
+  int32_t tile;        // vertices / queue positions / nets per task
+  int32_t small_nch;   // a round of at most this many chunks runs as one task
+};
 }  // namespace bgpc
 
 struct bgpc_ctx {
@@ -122,6 +174,20 @@ struct bgpc_ctx {
   bgpc::Buf<int32_t> rsum;             // ... scan block sums
   bgpc::Buf<float> mpart;              // MLP gradient: per-block partial sums
   bgpc::Buf<float> mgrad;              // MLP gradient (train step)
+  // bgpc_color_batched, persistent engine: scratch pools over the whole batch
+  bgpc::Buf<int32_t> bW0, bW1, bstage, bown, bsown, bd2, bkofs, bbig, btcnt, btofs, bntag;
+  bgpc::Buf<uint8_t> blose, binW;
+  bgpc::Buf<bgpc::BatchDesc> bdesc;
+  bgpc::Buf<bgpc::BatchState> bst;
+  bgpc::Buf<bgpc::BatchStat> bstat;
+  bgpc::Buf<bgpc::BatchGlobal> bglob;
+  void *h_batch = nullptr;             // pinned staging: descriptors, state, global, statistics
+  size_t h_batch_cap = 0;
+  cudaStream_t bstream = nullptr;      // private stream (capturable) of the persistent launch
+  cudaEvent_t bev[4] = {nullptr, nullptr, nullptr, nullptr};
+  cudaGraphExec_t bexec = nullptr;     // captured launch of the last batch ...
+  unsigned long long bkey = 0;         // ... and the batch it belongs to
+  std::vector<std::pair<unsigned long long, int>> btuned;  // autotuned mapping per batch
   bgpc::DevScalars *dev = nullptr;     // device scalars
   std::vector<cudaEvent_t> events;     // phase timing (opts.profile)
   bgpc::DevScalars *host = nullptr;    // pinned mirror
@@ -243,6 +309,19 @@ int launch_hub_select(const int32_t *b_ptr, int32_t n_b, int32_t H, int32_t *hub
                       int32_t *hub_net, DevScalars *dev, int sms, cudaStream_t s);
 int launch_hub_build(const int32_t *b_ptr, const int32_t *nc, const int32_t *hub_net,
                      int32_t nhub, int32_t words, uint32_t *nbm, int sms, cudaStream_t s);
+
+struct BatchLaunch {
+  const BatchDesc *desc;
+  BatchState *st;
+  BatchStat *stat;
+  BatchGlobal *glob;
+  int32_t G, C, Q, T, max_rounds, policy, sms;
+  int64_t timeout_ns;
+  BatchMapping map;
+  int32_t *W0, *W1, *stage, *own, *s_own, *d2, *kofs, *big, *tcnt, *tofs, *ntag;
+  uint8_t *lose, *inW;
+};
+cudaError_t launch_batch(const BatchLaunch &L, cudaStream_t s);
 
 // Wave of chunk j under Q waves: the Weyl sequence frac(j * phi), phi =
 // 0x9E3779B9 / 2^32, scaled to [0, Q).
