@@ -195,6 +195,7 @@ int color_impl(bgpc_ctx_t *ctx, const bgpc_graph_t &g, const bgpc_opts_t &o, int
   CU(grow(ctx->hub_id, (size_t)(n_b > 0 ? n_b : 1)));
   CU(grow(ctx->hub_net, (size_t)nnz / (kHubMin + 1) + 1));
   if (o.net_rounds > 0) CU(grow(ctx->netc, (size_t)n_a));
+  CU(grow(ctx->ihub, nz));
 
   // ---- setup (Alg. 1: W <- V_color, c <- -1), static graph analysis
   PhaseTimer tm(ctx, s, o.profile != 0);
@@ -203,11 +204,12 @@ int color_impl(bgpc_ctx_t *ctx, const bgpc_graph_t &g, const bgpc_opts_t &o, int
   CU(cudaMemsetAsync(ctx->dev, 0, sizeof(DevScalars), s));
   CU(cudaMemsetAsync(&ctx->dev->gmax, 0xff, sizeof(int32_t), s));
   CU(cudaMemsetAsync(ctx->lose.p, 0, (size_t)n_a, s));
-  nk += launch_tpos(g, ctx->tpos.p, &ctx->dev->err, sms, s);
+  nk += launch_hub_select(g.b_ptr, n_b, kHubMin, ctx->hub_id.p, ctx->hub_net.p, ctx->dev, sms, s);
+  nk += launch_tpos(g, ctx->tpos.p, &ctx->dev->err, ctx->hub_id.p,
+                    n_b > 0 ? ctx->ihub.p : nullptr, sms, s);
   nk += launch_vertex_static(g, ctx->tpos.p, ctx->s_own.p, ctx->d2tot.p, ctx->nown.p,
                              o.net_rounds > 0 ? ctx->netc.p : nullptr, center_first, sms, s);
   nk += launch_net_static(g, o.big_net, ctx->bigt.p, ctx->bigd.p, ctx->dev, s);
-  nk += launch_hub_select(g.b_ptr, n_b, kHubMin, ctx->hub_id.p, ctx->hub_net.p, ctx->dev, sms, s);
   nk += launch_init_queue(o.rank, n_a, ctx->W0.p, &ctx->dev->err, s);
   nk += launch_init_mirror(g, o.rank, ctx->nc.p, ctx->npos.p, colors, sms, s);
   tm.end(ev, PH_SETUP);
@@ -400,9 +402,9 @@ int color_impl(bgpc_ctx_t *ctx, const bgpc_graph_t &g, const bgpc_opts_t &o, int
         nk++;
         st.color_launches++;
         ev = tm.begin();
-        nk += launch_publish(g.a_ptr, g.a_idx, ctx->tpos.p, W, ctx->stage.p, wchunks, nwave, C,
-                             m, ctx->nc.p, colors, nhub > 0 ? ctx->hub_id.p : nullptr,
-                             ctx->nbm.p, words, ctx->dev, sms, s);
+        nk += launch_publish(g.a_ptr, nhub > 0 ? ctx->ihub.p : nullptr, ctx->tpos.p, W,
+                             ctx->stage.p, wchunks, nwave, C, m, ctx->nc.p, colors, ctx->nbm.p,
+                             words, ctx->dev, sms, s);
         tm.end(ev, PH_PUBLISH);
       }
       waves_done++;
@@ -870,7 +872,7 @@ int bgpc_ctx_destroy(bgpc_ctx_t *ctx) {
   release(ctx->tpos); release(ctx->nc); release(ctx->npos); release(ctx->nown);
   release(ctx->s_own); release(ctx->d2tot); release(ctx->W0); release(ctx->W1);
   release(ctx->kofs); release(ctx->stage); release(ctx->newpos); release(ctx->lose);
-  release(ctx->netc);
+  release(ctx->netc); release(ctx->ihub);
   release(ctx->blocksum); release(ctx->bigt); release(ctx->bigd);
   release(ctx->hub_id); release(ctx->hub_net); release(ctx->nbm);
   release(ctx->cptr); release(ctx->cidx); release(ctx->dtab); release(ctx->vtab);

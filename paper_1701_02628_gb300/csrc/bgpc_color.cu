@@ -1495,14 +1495,15 @@ __global__ void __launch_bounds__(kScanNT) k_piece_scatter(int32_t nslots,
 }
 
 // Publish: colors of the wave's positions go to c[] and to every CSC entry
-// of their edges (nc), and the running max color is updated.
-__global__ void k_publish(const int32_t *__restrict__ a_ptr, const int32_t *__restrict__ a_idx,
+// of their edges (nc), and the running max color is updated.  ihub[i] is the
+// hub slot of CSR entry i's net (-1: not a hub), read in CSR order instead of
+// looking the net up at random.
+__global__ void k_publish(const int32_t *__restrict__ a_ptr, const int32_t *__restrict__ ihub,
                           const int32_t *__restrict__ tpos,
                           const int32_t *__restrict__ W, const int32_t *__restrict__ stage,
                           const int32_t *__restrict__ chunks, int32_t nchunks, int32_t C,
                           int32_t m, int32_t *__restrict__ nc, int32_t *__restrict__ colors,
-                          const int32_t *__restrict__ hub_id, uint32_t *__restrict__ nbm,
-                          int32_t words, DevScalars *dev) {
+                          uint32_t *__restrict__ nbm, int32_t words, DevScalars *dev) {
   const int lane = threadIdx.x & 31;
   int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -1515,8 +1516,8 @@ __global__ void k_publish(const int32_t *__restrict__ a_ptr, const int32_t *__re
     const int32_t beg = a_ptr[w], end = a_ptr[w + 1];
     for (int32_t i = beg + lane; i < end; i += 32) {
       nc[tpos[i]] = col;
-      if (hub_id) {  // the color joins the bitmap of every hub net of w
-        const int32_t h = hub_id[a_idx[i]];
+      if (ihub) {  // the color joins the bitmap of every hub net of w
+        const int32_t h = ihub[i];
         if (h >= 0) atomicOr(&nbm[(int64_t)h * words + (col >> 5)], 1u << (col & 31));
       }
     }
@@ -1634,17 +1635,17 @@ int launch_pieces(const int32_t *a_ptr, const int32_t *d2tot, const int32_t *W,
   return 3;
 }
 
-int launch_publish(const int32_t *a_ptr, const int32_t *a_idx, const int32_t *tpos,
+int launch_publish(const int32_t *a_ptr, const int32_t *ihub, const int32_t *tpos,
                    const int32_t *W, const int32_t *stage, const int32_t *chunks,
                    int32_t nchunks, int32_t C, int32_t m, int32_t *nc, int32_t *colors,
-                   const int32_t *hub_id, uint32_t *nbm, int32_t words, DevScalars *dev,
-                   int sms, cudaStream_t s) {
+                   uint32_t *nbm, int32_t words, DevScalars *dev, int sms, cudaStream_t s) {
   if (nchunks <= 0) return 0;
   long long warps = (long long)nchunks * C;
   long long grid = div_up(warps * 32, 256);
-  if (grid > (long long)sms * 16) grid = (long long)sms * 16;
-  k_publish<<<(int)grid, 256, 0, s>>>(a_ptr, a_idx, tpos, W, stage, chunks, nchunks, C, m, nc,
-                                      colors, hub_id, nbm, words, dev);
+  // one resident set (8 CTAs of 256 per SM): no late second set as a tail
+  if (grid > (long long)sms * 8) grid = (long long)sms * 8;
+  k_publish<<<(int)grid, 256, 0, s>>>(a_ptr, ihub, tpos, W, stage, chunks, nchunks, C, m, nc,
+                                      colors, nbm, words, dev);
   return 1;
 }
 

@@ -405,7 +405,9 @@ __global__ void k_fill(int32_t *p, size_t n, int32_t v) {
 
 inline int warps_grid(long long items, int sms) {
   long long g = div_up(items * 32, kNT);
-  long long cap = (long long)sms * 16;
+  // one resident set of CTAs (8 of 256 threads per SM): every warp's share
+  // of the grid-stride loop starts at once, with no second set as a tail
+  long long cap = (long long)sms * 8;
   if (g > cap) g = cap;
   if (g < 1) g = 1;
   return (int)g;

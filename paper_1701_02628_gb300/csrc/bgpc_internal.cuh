@@ -145,6 +145,7 @@ struct bgpc_ctx {
   bgpc::Buf<uint8_t> nown;
   bgpc::Buf<int32_t> s_own, d2tot, W0, W1, kofs, stage, newpos;
   bgpc::Buf<int32_t> netc;             // net-based first round: proposal of the owner net
+  bgpc::Buf<int32_t> ihub;             // per CSR entry: hub slot of its net, or -1
   bgpc::Buf<uint8_t> lose;
   bgpc::Buf<int32_t> blocksum, bigt, bigd;
   bgpc::Buf<int32_t> wlist;            // chunks of the round ordered by wave
@@ -223,7 +224,8 @@ inline int div_up(long long a, long long b) { return (int)((a + b - 1) / b); }
 int launch_check_ptr(const int32_t *ptr, int32_t n, int32_t nnz, int32_t *err, cudaStream_t s);
 int launch_check_rows(const int32_t *ptr, const int32_t *idx, int32_t n, int32_t bound,
                        int32_t *err, int sms, cudaStream_t s);
-int launch_tpos(const bgpc_graph_t &g, int32_t *tpos, int32_t *err, int sms, cudaStream_t s);
+int launch_tpos(const bgpc_graph_t &g, int32_t *tpos, int32_t *err, const int32_t *hub_id,
+                int32_t *ihub, int sms, cudaStream_t s);
 int launch_vertex_static(const bgpc_graph_t &g, const int32_t *tpos, int32_t *s_own,
                           int32_t *d2tot, uint8_t *nown, int32_t *netc, int32_t center_first,
                           int sms, cudaStream_t s);
@@ -298,11 +300,10 @@ int launch_pieces(const int32_t *a_ptr, const int32_t *d2tot, const int32_t *W,
                   const int32_t *wlist, int32_t nch, int32_t C, int32_t m, int32_t small_ok,
                   int32_t *segoff, int32_t *blocksum, int2 *segmap, DevScalars *dev,
                   cudaStream_t s);
-int launch_publish(const int32_t *a_ptr, const int32_t *a_idx, const int32_t *tpos,
+int launch_publish(const int32_t *a_ptr, const int32_t *ihub, const int32_t *tpos,
                    const int32_t *W, const int32_t *stage, const int32_t *chunks,
                    int32_t nchunks, int32_t C, int32_t m, int32_t *nc, int32_t *colors,
-                   const int32_t *hub_id, uint32_t *nbm, int32_t words, DevScalars *dev,
-                   int sms, cudaStream_t s);
+                   uint32_t *nbm, int32_t words, DevScalars *dev, int sms, cudaStream_t s);
 // Per round: hub nets (more than H members) get a slot (hub_id, -1 otherwise)
 // and a color bitmap of their published members.
 int launch_hub_select(const int32_t *b_ptr, int32_t n_b, int32_t H, int32_t *hub_id,

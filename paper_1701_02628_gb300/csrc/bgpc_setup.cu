@@ -41,9 +41,11 @@ __global__ void k_check_rows(const int32_t *__restrict__ ptr, const int32_t *__r
 
 // tpos[i] = position of w inside vtxs(a_idx[i]) for CSR entry i of vertex w
 // (binary search in the sorted CSC column); a miss means CSR and CSC differ.
+// ihub[i] (when not NULL) = the hub slot of the net of CSR entry i, or -1.
 __global__ void k_tpos(const int32_t *__restrict__ a_ptr, const int32_t *__restrict__ a_idx,
                        const int32_t *__restrict__ b_ptr, const int32_t *__restrict__ b_idx,
-                       int32_t n_a, int32_t *__restrict__ tpos, int32_t *err) {
+                       int32_t n_a, int32_t *__restrict__ tpos, int32_t *err,
+                       const int32_t *__restrict__ hub_id, int32_t *__restrict__ ihub) {
   const int lane = threadIdx.x & 31;
   int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -51,6 +53,7 @@ __global__ void k_tpos(const int32_t *__restrict__ a_ptr, const int32_t *__restr
     int32_t beg = a_ptr[w], end = a_ptr[w + 1];
     for (int32_t i = beg + lane; i < end; i += 32) {
       int32_t v = a_idx[i];
+      if (ihub) ihub[i] = hub_id[v];
       int32_t lo = b_ptr[v], hi = b_ptr[v + 1];
       // first index of vtxs(v) holding an id >= w: a few interpolation
       // steps on the ids at the ends of the range (the members of a net are
@@ -257,10 +260,11 @@ int launch_check_rows(const int32_t *ptr, const int32_t *idx, int32_t n, int32_t
   return 1;
 }
 
-int launch_tpos(const bgpc_graph_t &g, int32_t *tpos, int32_t *err, int sms, cudaStream_t s) {
+int launch_tpos(const bgpc_graph_t &g, int32_t *tpos, int32_t *err, const int32_t *hub_id,
+                int32_t *ihub, int sms, cudaStream_t s) {
   if (g.n_a <= 0) return 0;
   k_tpos<<<grid_warps(g.n_a, sms), kNT, 0, s>>>(g.a_ptr, g.a_idx, g.b_ptr, g.b_idx, g.n_a,
-                                                 tpos, err);
+                                                 tpos, err, hub_id, ihub);
   return 1;
 }
 
