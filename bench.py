@@ -393,7 +393,25 @@ def learned_order_report(bg, ctx, dev, chung_lu_dg):
         std_l.append(b["std_card"] / b["mean_card"])
         t_id += ta
         t_l += tb
+    # the three orders side by side on 16 fresh graphs (|V_A| up to 1e5: the
+    # smallest-last order is built by one host thread)
+    cmp_n, cmp_sl, cmp_l, t_sl = [], [], [], 0.0
+    for i in range(16):
+        dg = bg.DeviceGraph.from_host(gg.batch_graph(29, 100 + i, lo=1e3, hi=1e5), dev)
+        cmp_n.append(id_run(dg)["colors"])
+        t0 = time.time()
+        srank, _ = bg.sl_rank(ctx, dg)
+        t_sl += time.time() - t0
+        cmp_sl.append(bg.bgpc_color(ctx, dg, rank=srank)[1]["colors"])
+        cmp_l.append(learned_run(dg)["colors"])
+    orders = {"graphs": 16, "colors_natural_mean": float(np.mean(cmp_n)),
+              "colors_smallest_last_mean": float(np.mean(cmp_sl)),
+              "colors_learned_mean": float(np.mean(cmp_l)),
+              "smallest_last_fewer_than_natural": int(sum(a < b for a, b in zip(cmp_sl, cmp_n))),
+              "learned_fewer_than_natural": int(sum(a < b for a, b in zip(cmp_l, cmp_n))),
+              "smallest_last_host_seconds": t_sl}
     return {"model": "MLP 8-64-64-1, bf16 weights, fp32 arithmetic, Adam",
+            "orders_compared": orders,
             "train": {"graphs": 16, "steps": len(losses), "loss_first": losses[0],
                       "loss_last": losses[-1], "seconds": t_train},
             "chung_lu_2^22": cl,

@@ -321,6 +321,20 @@ int bgpc_mlp_train_step(bgpc_ctx_t *ctx, bgpc_mlp_t *mlp, const float *X, const 
 int bgpc_rank_from_scores(bgpc_ctx_t *ctx, const float *score, int32_t n, int32_t *rank,
                           void *stream);
 
+/* Smallest-last order (the static order of Sec. VI, Tables II and IV) as a
+ * rank for bgpc_color: on the conflict graph (u ~ w iff they share a net) the
+ * vertices are removed one at a time, always a remaining vertex of smallest
+ * remaining degree (ties: the smallest id), and rank[w] = the position of w in
+ * the reverse removal order.  Each removal depends on all the earlier ones,
+ * so the order is built by one host thread (the graph is copied from the
+ * device; O(E2 log n) time); the coloring in that order runs on the GPU.
+ * rank: device int32 [n_a]; *degeneracy (host, may be NULL) = the largest
+ * degree at removal (first fit in this order uses at most degeneracy + 1
+ * colors).  BGPC_ENOMEM if the conflict graph has more than max_pairs
+ * (distinct ordered) neighbour pairs.  Synchronises `stream`. */
+int bgpc_rank_smallest_last(bgpc_ctx_t *ctx, const bgpc_graph_t *g, int64_t max_pairs,
+                            int32_t *rank, int32_t *degeneracy, void *stream);
+
 /* Human-readable text of a status code (static storage). */
 const char *bgpc_strerror(int status);
 

@@ -64,6 +64,7 @@ def _load():
         "orc_closed_nbhd": ([i32, P, P, P, P], ctypes.c_int),
         "orc_d2_conflicts": ([i32, P, P, P], i64),
         "orc_color_sets": ([i32, P, P, P64], i32),
+        "orc_sl_rank": (G + [P, P], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -189,6 +190,17 @@ def closed_nbhd(ug):
 def d2_conflicts(ug, c) -> int:
     """Vertices uncolored or sharing a color within shortest-path distance 2."""
     return int(_load().orc_d2_conflicts(int(ug.n), _p(ug.ptr), _p(ug.idx), _p(_i32(c))))
+
+
+def sl_rank(g):
+    """Smallest-last order (Sec. VI, Tables II / IV) on the conflict graph:
+    (rank, degeneracy); rank[w] = position of w in the coloring order."""
+    rank = np.empty(max(g.n_a, 1), np.int32)
+    dg = ctypes.c_int32(0)
+    rc = _load().orc_sl_rank(*_g(g), _p(rank), ctypes.byref(dg))
+    if rc != OK:
+        raise ValueError(f"orc_sl_rank failed: {rc}")
+    return rank[:g.n_a], dg.value
 
 
 def color_sets(c):

@@ -755,3 +755,55 @@ int32_t orc_color_sets(int32_t n, const int32_t *c, int32_t *n_sets, int64_t *ca
     }
     return mx;
 }
+
+/* ------------------------------------------------------------------------
+ * Smallest-last order (the static order of Table II and Table IV, Sec. VI)
+ * on the conflict graph of BGPC: u ~ w iff they share a net.  Repeatedly
+ * remove, among the vertices not yet removed, one of smallest degree in the
+ * remaining conflict graph (ties: the smallest id); the coloring order is the
+ * reverse of the removal order, rank[w] = its position in the coloring order.
+ * Plain O(n^2 + E2) version for small graphs: degrees are distinct two-hop
+ * neighbour counts, the minimum is found by a scan.  *degeneracy (if not
+ * NULL) = the largest degree a vertex had when it was removed.
+ * ---------------------------------------------------------------------- */
+int orc_sl_rank(int32_t n_a, int32_t n_b, const int32_t *a_ptr, const int32_t *a_idx,
+                const int32_t *b_ptr, const int32_t *b_idx, int32_t *rank,
+                int32_t *degeneracy) {
+    (void)n_b;
+    if (n_a < 0) return ORC_EINVAL;
+    int32_t *deg = (int32_t *)malloc(sizeof(int32_t) * ((size_t)n_a + 1));
+    int32_t *mark = (int32_t *)malloc(sizeof(int32_t) * ((size_t)n_a + 1));
+    uint8_t *gone = (uint8_t *)calloc((size_t)n_a + 1, 1);
+    if (!deg || !mark || !gone) { free(deg); free(mark); free(gone); return ORC_ENOMEM; }
+    for (int32_t u = 0; u < n_a; u++) mark[u] = -1;
+    for (int32_t w = 0; w < n_a; w++) {
+        int32_t cnt = 0;
+        for (int32_t e = a_ptr[w]; e < a_ptr[w + 1]; e++)
+            for (int32_t f = b_ptr[a_idx[e]]; f < b_ptr[a_idx[e] + 1]; f++) {
+                int32_t u = b_idx[f];
+                if (u != w && mark[u] != w) { mark[u] = w; cnt++; }
+            }
+        deg[w] = cnt;
+    }
+    int32_t dg = 0;
+    for (int32_t step = 0; step < n_a; step++) {
+        int32_t best = -1;
+        for (int32_t w = 0; w < n_a; w++)
+            if (!gone[w] && (best < 0 || deg[w] < deg[best])) best = w;
+        if (deg[best] > dg) dg = deg[best];
+        gone[best] = 1;
+        rank[best] = n_a - 1 - step;
+        /* every remaining distinct neighbour loses one degree */
+        for (int32_t e = a_ptr[best]; e < a_ptr[best + 1]; e++)
+            for (int32_t f = b_ptr[a_idx[e]]; f < b_ptr[a_idx[e] + 1]; f++) {
+                int32_t u = b_idx[f];
+                if (u != best && !gone[u] && mark[u] != n_a + best) {
+                    mark[u] = n_a + best;
+                    deg[u]--;
+                }
+            }
+    }
+    if (degeneracy) *degeneracy = dg;
+    free(deg); free(mark); free(gone);
+    return ORC_OK;
+}

@@ -109,4 +109,13 @@ int64_t orc_d2_conflicts(int32_t n, const int32_t *ptr, const int32_t *idx, cons
  * to only get K).  Returns the largest color, or -1. */
 int32_t orc_color_sets(int32_t n, const int32_t *c, int32_t *n_sets, int64_t *card);
 
+/* Smallest-last order (Sec. VI, Tables II and IV) on the conflict graph
+ * (u ~ w iff they share a net): remove, one at a time, a remaining vertex of
+ * smallest remaining degree (ties: smallest id); rank[w] = position of w in
+ * the reverse of the removal order (the coloring order).  *degeneracy (may be
+ * NULL) = the largest degree at removal.  O(n^2 + E2): small graphs only. */
+int orc_sl_rank(int32_t n_a, int32_t n_b, const int32_t *a_ptr, const int32_t *a_idx,
+                const int32_t *b_ptr, const int32_t *b_idx, int32_t *rank,
+                int32_t *degeneracy);
+
 #endif

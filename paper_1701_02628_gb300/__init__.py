@@ -79,7 +79,8 @@ class bgpc_stats_t(ctypes.Structure):
 EXPORTS = ["bgpc_opts_default", "bgpc_ctx_create", "bgpc_ctx_destroy", "bgpc_color",
            "bgpc_color_batched", "d2gc_color", "bgpc_validate", "bgpc_color_sets", "bgpc_color_sets_noalloc",
            "bgpc_features", "bgpc_mlp_sync", "bgpc_mlp_forward", "bgpc_mlp_grad",
-           "bgpc_mlp_adam", "bgpc_mlp_train_step", "bgpc_rank_from_scores", "bgpc_strerror"]
+           "bgpc_mlp_adam", "bgpc_mlp_train_step", "bgpc_rank_from_scores", "bgpc_strerror",
+           "bgpc_rank_smallest_last"]
 MLP_IN, MLP_HIDDEN, MLP_PARAMS = 8, 64, 4801
 
 
@@ -136,6 +137,9 @@ def load():
     lib.bgpc_mlp_adam.argtypes = [vp, M, vp, ctypes.c_float, vp]
     lib.bgpc_mlp_train_step.argtypes = [vp, M, vp, vp, ctypes.c_int32, ctypes.c_float, fp, vp]
     lib.bgpc_rank_from_scores.argtypes = [vp, vp, ctypes.c_int32, vp, vp]
+    lib.bgpc_rank_smallest_last.argtypes = [vp, ctypes.POINTER(bgpc_graph_t), ctypes.c_int64,
+                                            vp, _c_i32p, vp]
+    lib.bgpc_rank_smallest_last.restype = ctypes.c_int
     for name in ("bgpc_features", "bgpc_mlp_sync", "bgpc_mlp_forward", "bgpc_mlp_grad",
                  "bgpc_mlp_adam", "bgpc_mlp_train_step", "bgpc_rank_from_scores"):
         getattr(lib, name).restype = ctypes.c_int
@@ -484,6 +488,17 @@ def rank_from_scores(ctx: Context, score: torch.Tensor, out=None, stream=None):
                                         _ptr(r) if n else None, _stream(stream)),
            "bgpc_rank_from_scores")
     return r
+
+
+def sl_rank(ctx: Context, g: DeviceGraph, max_pairs: int = 1 << 31, stream=None):
+    """Smallest-last rank (bgpc_rank_smallest_last): (rank tensor, degeneracy)."""
+    rank = torch.empty(max(g.n_a, 1), dtype=torch.int32, device=g.a_ptr.device)
+    dg = ctypes.c_int32(0)
+    gs = g.c_struct()
+    _check(load().bgpc_rank_smallest_last(ctx.handle, ctypes.byref(gs), max_pairs,
+                                          _ptr(rank), ctypes.byref(dg), _stream(stream)),
+           "bgpc_rank_smallest_last")
+    return rank[:g.n_a], dg.value
 
 
 def learned_rank(ctx: Context, g: DeviceGraph, mlp: MLP, big_net: int = 64, stream=None):

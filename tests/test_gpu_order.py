@@ -261,3 +261,25 @@ def test_learned_order_gains_over_id_order(bg, ctx):
         tot_l += st_l["colors"]
     assert fewer >= 16 and more <= 3, (fewer, more)
     assert tot_l < tot_id
+
+
+def test_smallest_last_rank(bg, ctx):
+    """The library's smallest-last order is the oracle's (same definition,
+    separate code), and the GPU coloring in that order is the oracle's RS
+    coloring in that rank; the pair cap is enforced."""
+    dev = "cuda:0"
+    graphs = [gg.from_nets(4, [[0, 1], [0, 2], [0, 3]]), gg.random_bipartite(800, 500, 4, seed=3),
+              gg.stencil9(24), gg.chung_lu(3000, 10, 400, 2.1, seed=6),
+              gg.batch_graph(29, 0, lo=1e3, hi=3e3), gg.from_nets(6, [[0, 1], [], [3, 4]])]
+    for g in graphs:
+        dg = bg.DeviceGraph.from_host(g, dev)
+        rank, deg = bg.sl_rank(ctx, dg)
+        ref, rdeg = O.sl_rank(g)
+        assert np.array_equal(rank.cpu().numpy(), ref) and deg == rdeg
+        col, st, _ = bg.bgpc_color(ctx, dg, rank=rank)
+        rs = O.rs_color(g, rank=ref, nthreads=8)
+        assert np.array_equal(col.cpu().numpy(), rs.colors)
+    dg = bg.DeviceGraph.from_host(gg.random_bipartite(800, 500, 4, seed=3), dev)
+    with pytest.raises(bg.BgpcError) as e:
+        bg.sl_rank(ctx, dg, max_pairs=100)
+    assert e.value.status == bg.BGPC_ENOMEM

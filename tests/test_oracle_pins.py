@@ -513,3 +513,55 @@ def test_net_round_d2gc_valid_by_distance():
     for pol in POLICIES:
         r = O.rs_color(cn, pol, chunk=8, waves=4, big_net=16, net_rounds=1, center_first=True)
         assert r.status == O.OK and O.d2_conflicts(ug, r.colors) == 0
+
+
+# ------------------------------------------------------- smallest-last order
+
+def sl_py(n_a, nets):
+    """Smallest-last by its definition, with Python sets: remove a remaining
+    vertex of smallest remaining conflict degree (ties: smallest id); the
+    coloring order is the reverse removal order."""
+    nb = [set() for _ in range(n_a)]
+    for mem in nets:
+        for u in mem:
+            nb[u].update(x for x in mem if x != u)
+    left, removal = set(range(n_a)), []
+    while left:
+        w = min(left, key=lambda x: (len(nb[x] & left), x))
+        removal.append(w)
+        left.remove(w)
+    rank = [0] * n_a
+    for pos, w in enumerate(reversed(removal)):
+        rank[w] = pos
+    return rank
+
+
+def test_sl_hand_derived():
+    """Path 0-1-2-3 (conflict graph): degrees 1,2,2,1, removal 0,1,2,3, so the
+    coloring order is 3,2,1,0.  Star with center 0 and leaves 1,2,3: remove 1
+    (degree 1), then 2; the center and 3 now both have degree 1, the smaller
+    id (0) goes first, then 3: coloring order 3,0,2,1."""
+    r, dg = O.sl_rank(gg.from_nets(4, [[0, 1], [1, 2], [2, 3]]))
+    assert r.tolist() == [3, 2, 1, 0] and dg == 1
+    r, dg = O.sl_rank(gg.from_nets(4, [[0, 1], [0, 2], [0, 3]]))
+    assert r.tolist() == [1, 3, 2, 0] and dg == 1
+    r, dg = O.sl_rank(gg.from_nets(5, [list(range(5))]))  # a clique: ids in order
+    assert r.tolist() == [4, 3, 2, 1, 0] and dg == 4
+
+
+def test_sl_matches_definition_and_degeneracy_bound():
+    """Against the set-based statement on random tiny graphs; first fit in
+    smallest-last order uses at most degeneracy + 1 colors (every vertex has
+    at most `degeneracy` neighbours colored before it)."""
+    rng = np.random.default_rng(51)
+    for _ in range(40):
+        n_a, n_b = int(rng.integers(1, 30)), int(rng.integers(1, 20))
+        g, nets = random_tiny(rng, n_a, n_b, 6)
+        r, dg = O.sl_rank(g)
+        assert r.tolist() == sl_py(n_a, nets)
+        assert sorted(r.tolist()) == list(range(n_a))
+        c = O.seq_color(g, O.FF, rank=r)
+        assert O.conflicts(g, c) == 0 and c.max() + 1 <= dg + 1
+    g = gg.random_bipartite(400, 300, 4, seed=5)
+    r, dg = O.sl_rank(g)
+    assert O.seq_color(g, O.FF, rank=r).max() + 1 <= dg + 1
