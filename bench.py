@@ -62,6 +62,9 @@ WORKLOADS = {
     # the batched configuration: 512 independent graphs, one bgpc_color_batched call
     "batch512": ("512 graphs, |V_A| log-uniform [1e3,1e6], |V_B| = |V_A|*U[0.5,2], degree "
                  "Poisson(8) clipped to [1,64]; RS(64,16,64) first fit, id order, one batched call"),
+    # the first 128 graphs of the same batch, for profiler captures
+    "batch128": ("128 graphs of the batched workload (the first 128 of batch512), one batched "
+                 "call"),
 }
 
 
@@ -75,6 +78,8 @@ def make_workload(name="jacobian"):
         return [gg.chung_lu(1 << 22, 16.0, 50000.0, 2.1, seed=2)]
     if name == "batch512":
         return [gg.batch_graph(17, i) for i in range(512)]
+    if name == "batch128":
+        return [gg.batch_graph(17, i) for i in range(128)]
     if name == "rmat22":
         return [gg.rmat(22, 16, seed=3)]
     return [gg.stencil9(1024), gg.chung_lu(1 << 22, 16.0, 50000.0, 2.1, seed=2)]
@@ -524,7 +529,7 @@ def run_gpu(args):
     colors = [torch.empty(n_of(g), dtype=torch.int32, device=dev) for g in graphs]
     stream = torch.cuda.current_stream()
 
-    batched = args.workload == "batch512"
+    batched = args.workload.startswith("batch")
 
     last_rounds = []
 

@@ -160,13 +160,19 @@ typedef struct {
     int64_t kernel_launches;              /* kernels this call launched */
     int64_t color_launches;               /* wave-coloring kernel launches */
     double ms_setup, ms_color, ms_publish, ms_detect, ms_gather; /* device time per phase (profile) */
-    int64_t trav_hub;    /* all rounds: the part of trav_large in hub nets (more than 1024
-                            members), read from per-net color bitmaps instead of streamed */
+    int64_t trav_hub;    /* all rounds: the part of trav_large in hub nets (more than
+                            hub_threshold members), read from per-net color bitmaps instead
+                            of streamed */
     int64_t hub_pairs;   /* all rounds: (vertex, hub net) pairs so read */
     int64_t hub_words;   /* all rounds: bitmap words so read (under first fit a one-piece
                             vertex reads only the words its summary needs) */
     double ms_total;     /* host wall-clock time of the whole call (it synchronises its
                             stream, so this covers all of its device work) */
+    int32_t hub_threshold; /* nets with more members are hubs: the smallest of 512 * 2^(k/2)
+                              whose hubs' first-round bitmaps fit in half the L2 cache
+                              (INT32_MAX: no net qualifies); batched calls: the
+                              smallest over the graphs */
+    int32_t hubs;        /* hub nets (batched calls: summed over the graphs) */
 } bgpc_stats_t;
 
 /* Fill `opts` with the defaults: FF, C=64, Q=16, T=64, id order,

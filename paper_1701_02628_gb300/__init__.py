@@ -73,7 +73,8 @@ class bgpc_stats_t(ctypes.Structure):
                 ("ms_publish", ctypes.c_double), ("ms_detect", ctypes.c_double),
                 ("ms_gather", ctypes.c_double), ("trav_hub", ctypes.c_int64),
                 ("hub_pairs", ctypes.c_int64), ("hub_words", ctypes.c_int64),
-                ("ms_total", ctypes.c_double)]
+                ("ms_total", ctypes.c_double), ("hub_threshold", ctypes.c_int32),
+                ("hubs", ctypes.c_int32)]
 
 
 EXPORTS = ["bgpc_opts_default", "bgpc_ctx_create", "bgpc_ctx_destroy", "bgpc_color",
@@ -303,7 +304,7 @@ def stats_dict(st: bgpc_stats_t) -> dict:
                 color_launches=st.color_launches, ms_setup=st.ms_setup, ms_color=st.ms_color,
                 ms_publish=st.ms_publish, ms_detect=st.ms_detect, ms_gather=st.ms_gather,
                 trav_hub=st.trav_hub, hub_pairs=st.hub_pairs, hub_words=st.hub_words,
-                ms_total=st.ms_total)
+                ms_total=st.ms_total, hub_threshold=st.hub_threshold, hubs=st.hubs)
 
 
 def bgpc_color(ctx: Context, g: DeviceGraph, colors: torch.Tensor = None, stream=None, **opts):

@@ -163,6 +163,7 @@ int color_impl(bgpc_ctx_t *ctx, const bgpc_graph_t &g, const bgpc_opts_t &o, int
                int32_t center_first = 0) {
   bgpc_stats_t st;
   memset(&st, 0, sizeof(st));
+  st.hub_threshold = INT32_MAX;
   const int32_t n_a = g.n_a, n_b = g.n_b, nnz = g.nnz;
   const int sms = ctx->num_sms;
   if (n_a == 0) {
@@ -204,12 +205,14 @@ int color_impl(bgpc_ctx_t *ctx, const bgpc_graph_t &g, const bgpc_opts_t &o, int
   CU(cudaMemsetAsync(ctx->dev, 0, sizeof(DevScalars), s));
   CU(cudaMemsetAsync(&ctx->dev->gmax, 0xff, sizeof(int32_t), s));
   CU(cudaMemsetAsync(ctx->lose.p, 0, (size_t)n_a, s));
-  nk += launch_hub_select(g.b_ptr, n_b, kHubMin, ctx->hub_id.p, ctx->hub_net.p, ctx->dev, sms, s);
+  nk += launch_net_static(g, o.big_net, ctx->bigt.p, ctx->bigd.p, ctx->dev, s);
+  // hub bitmaps: at most half the L2 cache in the first round
+  nk += launch_hub_select(g.b_ptr, n_b, o.chunk, o.waves, (int64_t)ctx->l2_bytes / 8,
+                          ctx->hub_id.p, ctx->hub_net.p, ctx->dev, sms, s);
   nk += launch_tpos(g, ctx->tpos.p, &ctx->dev->err, ctx->hub_id.p,
                     n_b > 0 ? ctx->ihub.p : nullptr, sms, s);
   nk += launch_vertex_static(g, ctx->tpos.p, ctx->s_own.p, ctx->d2tot.p, ctx->nown.p,
                              o.net_rounds > 0 ? ctx->netc.p : nullptr, center_first, sms, s);
-  nk += launch_net_static(g, o.big_net, ctx->bigt.p, ctx->bigd.p, ctx->dev, s);
   nk += launch_init_queue(o.rank, n_a, ctx->W0.p, &ctx->dev->err, s);
   nk += launch_init_mirror(g, o.rank, ctx->nc.p, ctx->npos.p, colors, sms, s);
   tm.end(ev, PH_SETUP);
@@ -221,6 +224,8 @@ int color_impl(bgpc_ctx_t *ctx, const bgpc_graph_t &g, const bgpc_opts_t &o, int
   const int32_t nbig_t = ctx->host->nbig_t, nbig_d = ctx->host->nbig_d;
   const int32_t nhub = ctx->host->nhub;
   const int32_t maxnet = ctx->host->maxnet;
+  if (n_b > 0) st.hub_threshold = ctx->host->hub_H;
+  st.hubs = nhub;
   const int32_t max_words = wave_max_words(ctx->smem_optin);
 
   int32_t *W = ctx->W0.p, *Wn = ctx->W1.p;
@@ -773,6 +778,7 @@ int batch_persistent(bgpc_ctx_t *ctx, int32_t G, const bgpc_graph_t *graphs,
   // per-graph outcome: done, or handed to the single-graph engine
   bgpc_stats_t tot;
   memset(&tot, 0, sizeof(tot));
+  tot.hub_threshold = INT32_MAX;  // the persistent kernel keeps no hub bitmaps
   tot.kernel_launches = 1;
   tot.color_launches = 1;
   tot.ms_color = o.profile ? ms_k : 0.0;
@@ -795,6 +801,9 @@ int batch_persistent(bgpc_ctx_t *ctx, int32_t G, const bgpc_graph_t *graphs,
       tot.incid_total += one.incid_total;
       tot.w_total += one.w_total;
       tot.kernel_launches += one.kernel_launches;
+      tot.hub_threshold = one.hub_threshold < tot.hub_threshold ? one.hub_threshold
+                                                                : tot.hub_threshold;
+      tot.hubs += one.hubs;
       tot.pieces_total++;  // graphs handed to the single-graph engine
     } else if (status != kBatchDone) {
       return BGPC_EINTERNAL;
@@ -855,6 +864,7 @@ int bgpc_ctx_create(bgpc_ctx_t **out, int device) {
           cudaSuccess ||
       cudaDeviceGetAttribute(&ctx->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin,
                              device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&ctx->l2_bytes, cudaDevAttrL2CacheSize, device) != cudaSuccess ||
       cudaMalloc((void **)&ctx->dev, sizeof(DevScalars)) != cudaSuccess ||
       cudaMallocHost((void **)&ctx->host, sizeof(DevScalars)) != cudaSuccess) {
     cudaGetLastError();
@@ -1012,8 +1022,12 @@ int bgpc_color_batched(bgpc_ctx_t *ctx, int32_t n_graphs, const bgpc_graph_t *gr
   if (err.load() != 0) return err.load();
   bgpc_stats_t tot;
   memset(&tot, 0, sizeof(tot));
+  tot.hub_threshold = INT32_MAX;
   for (int32_t k = 0; k < n_graphs; k++) {
     const bgpc_stats_t &st = per[(size_t)k];
+    tot.hub_threshold = st.hub_threshold < tot.hub_threshold ? st.hub_threshold
+                                                             : tot.hub_threshold;
+    tot.hubs += st.hubs;
     if (rounds_out) rounds_out[k] = st.rounds;
     if (ncolors_out) ncolors_out[k] = st.colors;
     tot.rounds = st.rounds > tot.rounds ? st.rounds : tot.rounds;

@@ -956,14 +956,14 @@ __global__ void __launch_bounds__(NT) k_gather(GatherArgs a) {
   for (int32_t sg = sbeg + (int32_t)blockIdx.x; sg < send; sg += (int32_t)gridDim.x) {
     // ---- the piece: its vertex and the prefix of its net sizes
     if (warp == 0) {
-      const int2 sm = a.segmap[sg];
-      const int32_t u = sm.x, piece = sm.y;  // wave-order slot, piece of the vertex
+      // the piece's descriptor: wave-order slot, vertex, first incidence,
+      // number of nets | number of pieces of the vertex << 6
+      const int4 sm = a.segmap[sg];
+      const int32_t u = sm.x, w = sm.y, ibeg = sm.z;
+      const int32_t nnets = sm.w & 63, npieces = sm.w >> 6;
       const int32_t j = a.wlist[u / a.C];
       const int32_t p0 = j * a.C;
       const int32_t p = p0 + u % a.C;
-      const int32_t w = a.W[p];
-      const int32_t ibeg = a.a_ptr[w] + piece * kPiece;
-      const int32_t nnets = min(a.a_ptr[w + 1] - ibeg, kPiece);
       int32_t sz = 0, bp = 0, hub = -1;
       if (lane < nnets) {
         const int32_t v = a.a_idx[ibeg + lane];
@@ -996,11 +996,11 @@ __global__ void __launch_bounds__(NT) k_gather(GatherArgs a) {
         s_poff[0] = 0;
         s_info[0] = p0;
         s_info[1] = p - p0;
-        s_info[2] = (a.segoff[u + 1] - a.segoff[u]) == 1;
+        s_info[2] = npieces == 1;
         s_info[3] = nnets;
         s_info[4] = __popc(hubs);
         s_info[5] = w;
-        s_info[6] = a.segoff[u + 1] - a.segoff[u];
+        s_info[6] = npieces;
         s_slot = (int64_t)(u - a.slot_lo);
       }
     }
@@ -1203,14 +1203,22 @@ __global__ void __launch_bounds__(NT, 4) k_gather_w(GatherArgs a) {
   unsigned long long n_trav_hub = 0, n_hub_pairs = 0, n_hub_groups = 0;  // lane 0's counts
   for (int64_t sg = sbeg + (int64_t)blockIdx.x * NW + warp; sg < send; sg += nwarps) {
     // ---- the piece: its vertex, its chunk and its nets (one net per lane)
-    const int2 sm = a.segmap[sg];
-    const int32_t u = sm.x, piece = sm.y;
+    // the piece's descriptor (built by the piece map with full parallelism,
+    // so the warp starts with one load instead of a chain of four)
+    const int4 sm = a.segmap[sg];
+    const int32_t u = sm.x, w = sm.y, ibeg = sm.z;
+    const int32_t nnets = sm.w & 63, npieces = sm.w >> 6;
     const int32_t p0 = a.wlist[u / a.C] * a.C;
     const int32_t rel_hi = u % a.C;  // the vertex's index in its chunk
-    const int32_t w = a.W[p0 + rel_hi];
-    const int32_t ibeg = a.a_ptr[w] + piece * kPiece;
-    const int32_t nnets = min(a.a_ptr[w + 1] - ibeg, kPiece);
-    const bool whole = (a.segoff[u + 1] - a.segoff[u]) == 1;
+    const bool whole = npieces == 1;
+    // hub groups ORed here: all of them, except for a one-piece first-fit
+    // vertex, whose summary reads the groups up to its owner's top s - 1
+    // (and more only if its first 64 free colors lie beyond them)
+    int32_t so = 0, qor = W4;
+    if (a.summ && whole) {
+      so = a.s_own[w];
+      qor = min(W4, max(so > a.T ? ((so - 1) >> 7) + 1 : 0, 2));
+    }
     int32_t sz = 0, bp = 0, hub = -1, tp = 0;
     if (lane < nnets) {
       const int32_t v = a.a_idx[ibeg + lane];
@@ -1221,14 +1229,6 @@ __global__ void __launch_bounds__(NT, 4) k_gather_w(GatherArgs a) {
     }
     const unsigned hubs = __ballot_sync(kFull, hub >= 0);
     unsigned long long adj = 0ull;
-    // hub groups ORed here: all of them, except for a one-piece first-fit
-    // vertex, whose summary reads the groups up to its owner's top s - 1
-    // (and more only if its first 64 free colors lie beyond them)
-    int32_t so = 0, qor = W4;
-    if (a.summ && whole) {
-      so = a.s_own[w];
-      qor = min(W4, max(so > a.T ? ((so - 1) >> 7) + 1 : 0, 2));
-    }
     if (hubs) {
       n_trav_hub += (unsigned long long)__reduce_add_sync(kFull, hub >= 0 ? sz - 1 : 0);
       n_hub_pairs += (unsigned long long)__popc(hubs);
@@ -1327,13 +1327,17 @@ __global__ void __launch_bounds__(NT, 4) k_gather_w(GatherArgs a) {
       int32_t *rec = a.gsum + slot * kSumInts;
       int32_t got = 0, q0 = 0;
       warp_first_free_from<kSumCand>(s_bm, W4, qor, rec, got, q0);
-      if (got < kSumCand) {  // past the groups ORed so far: the rest of the hubs
-        if (hubs && qor < W4) {
-          warp_hub_or(s_bm4, nb4, W4, hubs, hub, qor, W4);
-          n_hub_groups += (unsigned long long)__popc(hubs) * (W4 - qor);
-        }
-        warp_first_free_from<kSumCand>(s_bm, W4, INT32_MAX, rec, got, q0);
+      // past the groups ORed so far: the hubs' next groups, twice as many
+      // each step, until 64 free colors are found (the streamed nets are
+      // complete at every group)
+      while (got < kSumCand && hubs && qor < W4) {
+        const int32_t qn = min(W4, 2 * qor);
+        warp_hub_or(s_bm4, nb4, W4, hubs, hub, qor, qn);
+        n_hub_groups += (unsigned long long)__popc(hubs) * (qn - qor);
+        qor = qn;
+        warp_first_free_from<kSumCand>(s_bm, W4, qor, rec, got, q0);
       }
+      if (got < kSumCand) warp_first_free_from<kSumCand>(s_bm, W4, INT32_MAX, rec, got, q0);
       warp_summarize_rest(s_bm, so, a.T, (so > a.T) ? a.kofs[p0 + rel_hi] : 0, adjm, rec,
                           a.lbm + slot * a.words);
       warp_clear(s_bm4, W4);
@@ -1365,7 +1369,7 @@ __global__ void __launch_bounds__(NT, 4) k_gather_w(GatherArgs a) {
       __threadfence();
       __syncwarp();
       int32_t last = 0;
-      if (lane == 0) last = atomicAdd(a.gcnt + slot, 1) == a.segoff[u + 1] - a.segoff[u] - 1;
+      if (lane == 0) last = atomicAdd(a.gcnt + slot, 1) == npieces - 1;
       last = __shfl_sync(kFull, last, 0);
       if (last) {
         __threadfence();
@@ -1472,7 +1476,11 @@ __global__ void __launch_bounds__(kScanNT) k_piece_blocks(int32_t *__restrict__ 
 __global__ void __launch_bounds__(kScanNT) k_piece_scatter(int32_t nslots,
                                                            const int32_t *__restrict__ blocksum,
                                                            int32_t *__restrict__ segoff,
-                                                           int2 *__restrict__ segmap) {
+                                                           int4 *__restrict__ segmap,
+                                                           const int32_t *__restrict__ a_ptr,
+                                                           const int32_t *__restrict__ W,
+                                                           const int32_t *__restrict__ wlist,
+                                                           int32_t C) {
   __shared__ int32_t red[kScanNT / 32];
   const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanPer;
   int32_t k[kScanPer];
@@ -1488,7 +1496,17 @@ __global__ void __launch_bounds__(kScanNT) k_piece_scatter(int32_t nslots,
   for (int q = 0; q < kScanPer; q++) {
     if (base + q < nslots) {
       segoff[base + q] = ex;
-      for (int32_t r = 0; r < k[q]; r++) segmap[ex + r] = make_int2((int32_t)(base + q), r);
+      if (k[q] > 0) {
+        // piece r of the vertex in slot u: {u, vertex, first incidence,
+        // nets | pieces << 6}
+        const int32_t u = (int32_t)(base + q);
+        const int32_t w = W[wlist[u / C] * C + u % C];
+        const int32_t ab = a_ptr[w], ae = a_ptr[w + 1];
+        for (int32_t r = 0; r < k[q]; r++) {
+          const int32_t ib = ab + r * kPiece;
+          segmap[ex + r] = make_int4(u, w, ib, min(ae - ib, kPiece) | (k[q] << 6));
+        }
+      }
       ex += k[q];
     }
   }
@@ -1623,7 +1641,7 @@ cudaError_t launch_gather(const GatherArgs &a, bool cta_only, int sms, cudaStrea
 
 int launch_pieces(const int32_t *a_ptr, const int32_t *d2tot, const int32_t *W,
                   const int32_t *wlist, int32_t nch, int32_t C, int32_t m, int32_t small_ok,
-                  int32_t *segoff, int32_t *blocksum, int2 *segmap, DevScalars *dev,
+                  int32_t *segoff, int32_t *blocksum, int4 *segmap, DevScalars *dev,
                   cudaStream_t s) {
   const int32_t nslots = nch * C;
   if (nslots <= 0) return 0;
@@ -1631,7 +1649,8 @@ int launch_pieces(const int32_t *a_ptr, const int32_t *d2tot, const int32_t *W,
   k_piece_count<<<nblocks, kScanNT, 0, s>>>(a_ptr, d2tot, W, wlist, nslots, C, m, small_ok,
                                             segoff, blocksum);
   k_piece_blocks<<<1, kScanNT, 0, s>>>(blocksum, nblocks, nslots, segoff, dev);
-  k_piece_scatter<<<nblocks, kScanNT, 0, s>>>(nslots, blocksum, segoff, segmap);
+  k_piece_scatter<<<nblocks, kScanNT, 0, s>>>(nslots, blocksum, segoff, segmap, a_ptr, W,
+                                              wlist, C);
   return 3;
 }
 
@@ -1651,9 +1670,28 @@ int launch_publish(const int32_t *a_ptr, const int32_t *ihub, const int32_t *tpo
 
 // ---------------------------------------------------------- hub nets
 // Nets with more than H members get a slot (order of the slots is irrelevant).
-__global__ void k_hub_select(const int32_t *__restrict__ b_ptr, int32_t n_b, int32_t H,
-                             int32_t *__restrict__ hub_id, int32_t *__restrict__ hub_net,
-                             DevScalars *dev) {
+// The hub threshold: the smallest ladder size whose nets' first-round bitmaps
+// (the round-0 width: every color <= max(maxnet - 1, 0) + C * Q) take at most
+// budget_words words; then hub_id[v] = the slot of net v if it is larger, or -1.
+__global__ void k_hub_select(const int32_t *__restrict__ b_ptr, int32_t n_b, int32_t C,
+                             int32_t Q, int64_t budget_words, int32_t *__restrict__ hub_id,
+                             int32_t *__restrict__ hub_net, DevScalars *dev) {
+  __shared__ int32_t s_H;
+  if (threadIdx.x == 0) {
+    const int64_t ncol = (int64_t)max(dev->maxnet - 1, 0) + (int64_t)C * Q + C + 2;
+    const int64_t words0 = ((ncol + 31) / 32 + 3) & ~(int64_t)3;
+    int32_t H = INT32_MAX;
+    int64_t above = 0;  // nets larger than hub_ladder(k)
+    for (int k = kHubLadder - 1; k >= 0; k--) {
+      above += dev->hub_hist[k];
+      if (above * words0 > budget_words) break;
+      H = hub_ladder(k);
+    }
+    s_H = H;
+    if (blockIdx.x == 0) dev->hub_H = H;
+  }
+  __syncthreads();
+  const int32_t H = s_H;
   for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n_b;
        v += (int64_t)gridDim.x * blockDim.x) {
     int32_t h = -1;
@@ -1689,12 +1727,13 @@ __global__ void __launch_bounds__(256) k_hub_build(const int32_t *__restrict__ b
   }
 }
 
-int launch_hub_select(const int32_t *b_ptr, int32_t n_b, int32_t H, int32_t *hub_id,
-                      int32_t *hub_net, DevScalars *dev, int sms, cudaStream_t s) {
+int launch_hub_select(const int32_t *b_ptr, int32_t n_b, int32_t C, int32_t Q,
+                      int64_t budget_words, int32_t *hub_id, int32_t *hub_net, DevScalars *dev,
+                      int sms, cudaStream_t s) {
   if (n_b <= 0) return 0;
   long long grid = div_up(n_b, 256);
   if (grid > (long long)sms * 8) grid = (long long)sms * 8;
-  k_hub_select<<<(int)grid, 256, 0, s>>>(b_ptr, n_b, H, hub_id, hub_net, dev);
+  k_hub_select<<<(int)grid, 256, 0, s>>>(b_ptr, n_b, C, Q, budget_words, hub_id, hub_net, dev);
   return 1;
 }
 

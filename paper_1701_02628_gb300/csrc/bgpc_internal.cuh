@@ -48,6 +48,15 @@ constexpr int kDetectWarpMax = 32;  // nets up to this size use the warp tier
 constexpr int kSumCand = 64;
 constexpr int kSumInts = 2 * kSumCand + 4;  // cand | rcand | rcnt, pad | adj (u64)
 
+// Hub nets (colors kept as bitmaps) have more members than a threshold taken
+// per call from the ladder kHubMin * 2^(k/2), k < kHubLadder: the smallest
+// one whose hubs' first-round bitmaps fit in half the L2 cache (bitmaps read
+// from L2 cost less than streaming the members' mirror words; once they spill
+// to DRAM they cost more).
+constexpr int32_t kHubMin = 512;
+constexpr int kHubLadder = 24;
+__host__ __device__ inline int32_t hub_ladder(int k) { return ((k & 1) ? 724 : 512) << (k >> 1); }
+
 // Device scalars shared by the kernels of one call.
 struct DevScalars {
   int32_t err;
@@ -68,11 +77,11 @@ struct DevScalars {
   unsigned long long hub_words;  // hub bitmap words ORed by those pairs
   unsigned long long acc[4]; // reductions (statistics)
   unsigned long long incid_next;  // sum over W_{r+1} of |nets(w)| (set by the compaction)
+  int32_t hub_hist[kHubLadder];   // nets with hub_ladder(k) < size <= hub_ladder(k + 1)
+  int32_t hub_H;                  // the hub threshold of the call
+  int32_t pad2;
 };
 constexpr int kRoundCounters = 8;  // trav .. hub_words, zeroed at the start of a round
-constexpr int32_t kHubMin = 1024;  // a hub net has more members than this and than the
-                                   // round's bitmap words
-
 template <typename T>
 struct Buf {
   T *p = nullptr;
@@ -141,6 +150,7 @@ struct bgpc_ctx {
   std::vector<cudaStream_t> sub_streams;
   int num_sms = 0;
   int smem_optin = 0;  // max dynamic shared memory per block (bytes)
+  int l2_bytes = 0;    // L2 cache size
   bgpc::Buf<int32_t> tpos, nc, npos;
   bgpc::Buf<uint8_t> nown;
   bgpc::Buf<int32_t> s_own, d2tot, W0, W1, kofs, stage, newpos;
@@ -150,7 +160,8 @@ struct bgpc_ctx {
   bgpc::Buf<int32_t> blocksum, bigt, bigd;
   bgpc::Buf<int32_t> wlist;            // chunks of the round ordered by wave
   bgpc::Buf<int32_t> segoff;           // gather pieces: exclusive prefix in wave order
-  bgpc::Buf<int2> segmap;              // gather piece -> (wave-order slot, piece index)
+  bgpc::Buf<int4> segmap;              // gather piece -> {slot, vertex, first incidence,
+                                       //   nets | pieces of the vertex << 6}
   bgpc::Buf<uint32_t> gbm;             // per-slot forbidden bitmaps of large vertices
   bgpc::Buf<int32_t> hub_id, hub_net;  // net -> hub slot (-1: not a hub), slot -> net
   bgpc::Buf<uint32_t> nbm;             // hub color bitmaps [nhub][words]
@@ -268,7 +279,7 @@ struct GatherArgs {
   const int32_t *nc;
   const int32_t *W;
   const int32_t *wlist;        // the round's chunks in wave order
-  const int2 *segmap;          // piece -> (wave-order slot, piece index)
+  const int4 *segmap;          // piece -> {slot, vertex, first incidence, nets | pieces << 6}
   const int32_t *segoff;       // exclusive prefix of pieces over wave-order slots
   int32_t m, C;
   int32_t slot_lo, slot_hi;    // wave-order slots of this wave
@@ -298,7 +309,7 @@ cudaError_t launch_gather(const GatherArgs &a, bool cta_only, int sms, cudaStrea
 // Per round: pieces per wave-order slot, their prefix and the piece map.
 int launch_pieces(const int32_t *a_ptr, const int32_t *d2tot, const int32_t *W,
                   const int32_t *wlist, int32_t nch, int32_t C, int32_t m, int32_t small_ok,
-                  int32_t *segoff, int32_t *blocksum, int2 *segmap, DevScalars *dev,
+                  int32_t *segoff, int32_t *blocksum, int4 *segmap, DevScalars *dev,
                   cudaStream_t s);
 int launch_publish(const int32_t *a_ptr, const int32_t *ihub, const int32_t *tpos,
                    const int32_t *W, const int32_t *stage, const int32_t *chunks,
@@ -306,8 +317,9 @@ int launch_publish(const int32_t *a_ptr, const int32_t *ihub, const int32_t *tpo
                    uint32_t *nbm, int32_t words, DevScalars *dev, int sms, cudaStream_t s);
 // Per round: hub nets (more than H members) get a slot (hub_id, -1 otherwise)
 // and a color bitmap of their published members.
-int launch_hub_select(const int32_t *b_ptr, int32_t n_b, int32_t H, int32_t *hub_id,
-                      int32_t *hub_net, DevScalars *dev, int sms, cudaStream_t s);
+int launch_hub_select(const int32_t *b_ptr, int32_t n_b, int32_t C, int32_t Q,
+                      int64_t budget_words, int32_t *hub_id, int32_t *hub_net, DevScalars *dev,
+                      int sms, cudaStream_t s);
 int launch_hub_build(const int32_t *b_ptr, const int32_t *nc, const int32_t *hub_net,
                      int32_t nhub, int32_t words, uint32_t *nbm, int sms, cudaStream_t s);
 

@@ -155,8 +155,9 @@ __global__ void k_vertex_static(const int32_t *__restrict__ a_ptr,
   }
 }
 
-// Largest net, and the lists of nets above T (reverse first fit) and above
-// the warp-detection size.  List order does not affect any result.
+// Largest net, the lists of nets above T (reverse first fit) and above the
+// warp-detection size, and the histogram of net sizes over the hub ladder.
+// List order does not affect any result.
 __global__ void k_net_static(const int32_t *__restrict__ b_ptr, int32_t n_b, int32_t T,
                              int32_t *__restrict__ bigt, int32_t *__restrict__ bigd,
                              DevScalars *dev) {
@@ -166,6 +167,11 @@ __global__ void k_net_static(const int32_t *__restrict__ b_ptr, int32_t n_b, int
     s = b_ptr[v + 1] - b_ptr[v];
     if (s > T) bigt[atomicAdd(&dev->nbig_t, 1)] = (int32_t)v;
     if (s > kDetectWarpMax) bigd[atomicAdd(&dev->nbig_d, 1)] = (int32_t)v;
+    if (s > kHubMin) {
+      int k = 0;
+      while (k + 1 < kHubLadder && hub_ladder(k + 1) < s) k++;
+      atomicAdd(&dev->hub_hist[k], 1);
+    }
   }
   for (int o = 16; o > 0; o >>= 1) s = max(s, __shfl_xor_sync(0xffffffffu, s, o));
   if ((threadIdx.x & 31) == 0 && s > 0) atomicMax(&dev->maxnet, s);

@@ -48,7 +48,7 @@ def test_host_only_calls(lib):
     assert (o.policy, o.chunk, o.waves, o.big_net, o.max_rounds) == (0, 64, 16, 64, 1000)
     assert bg.bgpc_strerror(bg.BGPC_EUNSORTED).startswith("adjacency")
     assert ctypes.sizeof(bg.bgpc_stats_t) == (4 + 4 + 8 * 64 * 2 + 8 + 4 * 4 + 8 * 2 + 8 * 4
-                                               + 8 * 4 + 8 * 5 + 8 * 3 + 8)
+                                               + 8 * 4 + 8 * 5 + 8 * 3 + 8 + 4 * 2)
 
 
 def test_struct_layout_matches_header():

@@ -15,6 +15,7 @@ import pytest
 import torch
 
 import graphgen as gg
+import hubrule
 import oracle as O
 import rs_py
 
@@ -129,6 +130,7 @@ def test_chung_lu_4m_sampled(bg, ctx):
     assert rc == bg.BGPC_OK
     assert per_net_valid(g.b_ptr, g.b_idx, g.n_b, colors.cpu().numpy())
     assert st["w_per_round"][0] == g.n_a
+    assert hubrule.check(st, np.diff(g.b_ptr)) == 512  # 10,755 hubs, 52 MB of bitmaps
 
 
 @pytest.mark.parametrize("policy", [O.FF, O.B1, O.B2])
@@ -143,6 +145,9 @@ def test_rmat22_d2gc_sampled(bg, ctx, rmat22, policy):
     colors, st, rc = run(policy=policy)
     assert rc == bg.BGPC_OK
     assert per_net_valid(cn.b_ptr, cn.b_idx, cn.n_b, colors.cpu().numpy())
+    # the bitmaps of the nets above 512 members would not fit in half the
+    # L2: the threshold is raised up the ladder
+    assert hubrule.check(st, np.diff(cn.b_ptr)) > 512
 
 
 def test_chung_lu_4m_net_round(bg, ctx):

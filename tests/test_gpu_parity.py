@@ -6,6 +6,7 @@ import pytest
 import torch
 
 import graphgen as gg
+import hubrule
 import oracle as O
 
 pytestmark = pytest.mark.gpu
@@ -83,7 +84,7 @@ def test_policies_power_law(bg, ctx, policy):
 
 
 def hub_graph():
-    """Three nets above the hub threshold (1024 members), overlapping, plus
+    """Three nets above the smallest hub threshold (512 members), overlapping, plus
     2500 small random nets: the members of a hub net gather it from its
     color bitmap and find their chunk-mates in it by binary search."""
     rng = np.random.default_rng(4)
@@ -97,9 +98,11 @@ def test_hub_nets(bg, ctx, policy):
     g = hub_graph()
     st = assert_parity(bg, ctx, g, policy=policy)
     assert st["hub_pairs"] > 0 and st["trav_hub"] > 0
-    g = gg.chung_lu(30000, 12, 6000, 2.1, seed=3)  # 17 nets above 1024 members
+    assert hubrule.check(st, np.diff(g.b_ptr)) == 512
+    g = gg.chung_lu(30000, 12, 6000, 2.1, seed=3)  # 47 nets above 512 members
     st = assert_parity(bg, ctx, g, policy=policy)
     assert st["hub_pairs"] > 0
+    assert hubrule.check(st, np.diff(g.b_ptr)) == 512 and st["hubs"] > 0
 
 
 @pytest.mark.parametrize("policy", [O.FF, O.B2])
