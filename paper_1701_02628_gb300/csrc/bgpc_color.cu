@@ -253,10 +253,8 @@ __device__ __forceinline__ int32_t win_kth_free_down(uint32_t word, int32_t top,
 // needs only the kSumCand smallest free colors of F_S, and the reverse first
 // fit needs the free colors of F_S from the k-th below the top on (plus, for
 // overlay colors above that window, one bit of g each).  The gather computes
-// these summaries from the bitmap in shared memory; the resolve keeps the
-// first kCand entries of each list in shared memory and reads the rest from
-// the summary only when its chunk-mates take all kCand.
-constexpr int kCand = 32;
+// these summaries from the bitmap in shared memory; the resolve keeps one
+// list per vertex (the reverse window when it has one) in shared memory.
 
 // The N smallest colors not in g, ascending, into out[].  g holds `words`
 // words (16-byte aligned, words a multiple of 4; colors beyond are free);
@@ -387,42 +385,9 @@ __device__ __forceinline__ void warp_summarize(const uint32_t *bm, int32_t words
   warp_summarize_rest(bm, so, T, k, adj, rec, lb);
 }
 
-// Index of the candidate equal to c in a sorted list (ascending if asc),
-// or -1.
-__device__ __forceinline__ int32_t cand_index(const int32_t *list, int32_t cnt, int32_t c,
-                                              bool asc) {
-  int32_t lo = 0, hi = cnt - 1;
-  while (lo < hi) {
-    const int32_t mid = (lo + hi) >> 1;
-    const bool before = asc ? (list[mid] < c) : (list[mid] > c);
-    if (before) lo = mid + 1; else hi = mid;
-  }
-  return (cnt > 0 && list[lo] == c) ? lo : -1;
-}
-
 __device__ __forceinline__ unsigned long long low_mask64(int32_t n) {
   return n >= 64 ? ~0ull : ((1ull << n) - 1ull);
 }
-
-// The entries of list[0, cnt) (sorted, ascending if asc) equal to one of the
-// warp's overlay colors oc[] that are not above hi, as a mask (the same in
-// every lane).
-__device__ __forceinline__ unsigned long long overlay_marks(const int32_t *list, int32_t cnt,
-                                                            const int32_t (&oc)[2], int32_t hi,
-                                                            bool asc) {
-  unsigned long long m = 0ull;
-#pragma unroll
-  for (int h = 0; h < 2; h++) {
-    const int32_t c = oc[h];
-    if (c < 0 || c > hi) continue;
-    const int32_t idx = cand_index(list, cnt, c, asc);
-    if (idx >= 0) m |= 1ull << idx;
-  }
-  const unsigned lo = __reduce_or_sync(kFull, (unsigned)(m & 0xffffffffull));
-  const unsigned hi32 = __reduce_or_sync(kFull, (unsigned)(m >> 32));
-  return ((unsigned long long)hi32 << 32) | lo;
-}
-
 
 // --------------------------------------------------------- resolve kernel
 
@@ -430,6 +395,271 @@ __device__ __forceinline__ unsigned long long overlay_marks(const int32_t *list,
 // piece count of k_piece_count).
 __device__ __forceinline__ bool is_small(int32_t d2, int32_t deg, bool small_ok) {
   return small_ok && d2 <= kSmallD2 && deg <= kSmallMaxDeg;
+}
+
+// Position of the set bit of v with n set bits below it (v has more than n).
+__device__ __forceinline__ int32_t nth_set_bit64(unsigned long long v, int32_t n) {
+  int32_t pos = 0;
+#pragma unroll
+  for (int w = 32; w > 0; w >>= 1) {
+    const int32_t c = __popcll(v & ((1ull << w) - 1ull));
+    if (n >= c) {
+      n -= c;
+      v >>= w;
+      pos += w;
+    }
+  }
+  return pos;
+}
+
+// The entries of the ascending list l[0, cnt) equal to one of the warp's keys
+// (two per lane; INT32_MIN: none), as a mask in every lane.  Both searches of
+// a lane run side by side.
+__device__ __forceinline__ unsigned long long list_marks(const int32_t *l, int32_t cnt,
+                                                         int32_t k0, int32_t k1) {
+  int32_t p0 = 0, p1 = 0;
+#pragma unroll
+  for (int w = 32; w > 0; w >>= 1) {
+    const bool g0 = p0 + w - 1 < cnt && l[p0 + w - 1] < k0;
+    const bool g1 = p1 + w - 1 < cnt && l[p1 + w - 1] < k1;
+    if (g0) p0 += w;
+    if (g1) p1 += w;
+  }
+  unsigned long long m = 0ull;
+  if (k0 != INT32_MIN && p0 < cnt && l[p0] == k0) m |= 1ull << p0;
+  if (k1 != INT32_MIN && p1 < cnt && l[p1] == k1) m |= 1ull << p1;
+  const unsigned lo = __reduce_or_sync(kFull, (unsigned)m);
+  const unsigned hi = __reduce_or_sync(kFull, (unsigned)(m >> 32));
+  return ((unsigned long long)hi << 32) | lo;
+}
+
+// The same mask through a scratch bitmap over the list's span (l[cnt - 1] -
+// l[0] < kPullBits, else by search): each lane sets the bits of its keys,
+// then tests the bits of its two entries.  The scratch is zero before and after.
+constexpr int kPullBits = 4096;
+__device__ __forceinline__ unsigned long long pull_marks(const int32_t *l, int32_t cnt,
+                                                         int32_t k0, int32_t k1,
+                                                         uint32_t *scr) {
+  const int lane = threadIdx.x & 31;
+  const int32_t b = l[0], span = l[cnt - 1] - b;
+  if (span >= kPullBits) return list_marks(l, cnt, k0, k1);
+  const int32_t e0 = lane < cnt ? l[lane] - b : -1;
+  const int32_t e1 = lane + 32 < cnt ? l[lane + 32] - b : -1;
+  // keys outside [b, b + span] take no entry (INT32_MIN: out of range)
+  const int32_t o0 = (k0 != INT32_MIN && k0 >= b && k0 - b <= span) ? k0 - b : -1;
+  const int32_t o1 = (k1 != INT32_MIN && k1 >= b && k1 - b <= span) ? k1 - b : -1;
+  if (o0 >= 0) atomicOr(&scr[o0 >> 5], 1u << (o0 & 31));
+  if (o1 >= 0) atomicOr(&scr[o1 >> 5], 1u << (o1 & 31));
+  __syncwarp();
+  const bool t0 = e0 >= 0 && ((scr[e0 >> 5] >> (e0 & 31)) & 1u);
+  const bool t1 = e1 >= 0 && ((scr[e1 >> 5] >> (e1 & 31)) & 1u);
+  const unsigned long long tk =
+      ((unsigned long long)__ballot_sync(kFull, t1) << 32) | __ballot_sync(kFull, t0);
+  if (o0 >= 0) scr[o0 >> 5] = 0u;
+  if (o1 >= 0) scr[o1 >> 5] = 0u;
+  __syncwarp();
+  return tk;
+}
+
+// First fit, phase B: one warp colors the chunk's vertices that have earlier
+// neighbours in the chunk, in order (a vertex's color depends on its earlier
+// neighbours' final colors, and on later rounds the chunks are nearly
+// complete chains).  Each large vertex has one ascending candidate list in
+// shared memory: its 64 smallest free colors, or its reverse first-fit window
+// negated.  Lane v % 32 keeps vertex v's color (col, once decided: dec) in a
+// register (slot v / 32).  At its step a vertex looks its neighbours' colors
+// up in its list (one search per neighbour, all in parallel): x = the first
+// entry none takes (first fit), or the (e+1)-th, where e counts the distinct
+// neighbour colors in (ak, so - 1] that are free in its forbidden set F_S
+// (reverse first fit: each shifts the k-th free color one further down).
+// Those F_S bits (fm, in shared memory) are pushed when a neighbour's color
+// is decided: the bitmap word is loaded then and folded in one step later, so
+// only the load for the immediately preceding vertex is waited for; dup
+// holds each vertex's earlier vertices of the same color (an overlay is a set).
+__device__ __forceinline__ void ff_walk(const WaveArgs &a, int32_t n, int64_t slot0,
+                                        unsigned long long large,
+                                        const unsigned long long *s_adj, int32_t *s_col,
+                                        uint32_t (*s_bm)[kWords], const int32_t *s_sown,
+                                        const int32_t *s_k, const int32_t (*s_list)[kSumCand],
+                                        const int32_t *s_rcnt, unsigned long long *s_dup,
+                                        unsigned long long *s_fm, int32_t *cx, uint32_t *wscr,
+                                        uint32_t *pscr) {
+  const int lane = threadIdx.x & 31;
+  unsigned long long adj[2];
+  int32_t col[2], lo[2], hi[2];
+  bool dec[2];
+  uint32_t pw[2];   // pending bitmap word of the last fm push
+  int32_t pbit[2];  // its bit (color & 31) and the pushing vertex: bit | j << 5, or -1
+#pragma unroll
+  for (int h = 0; h < 2; h++) {
+    const int32_t v = lane + 32 * h;
+    const bool valid = v < n;
+    const bool rff = valid && ((large >> v) & 1ull) && s_rcnt[v] > 0;
+    adj[h] = valid ? s_adj[v] : 0ull;
+    dec[h] = valid && adj[h] == 0ull;  // colored by step P
+    col[h] = dec[h] ? s_col[v] : -1;
+    lo[h] = rff ? -s_list[v][0] : INT32_MAX;  // fm tests colors in (lo, hi]
+    hi[h] = rff ? s_sown[v] - 1 : INT32_MIN;
+    if (valid) s_dup[v] = s_fm[v] = 0ull;
+    pw[h] = 0u;
+    pbit[h] = -1;
+  }
+  const unsigned long long decided0 =
+      ((unsigned long long)__ballot_sync(kFull, dec[1]) << 32) | __ballot_sync(kFull, dec[0]);
+  if (decided0 == low_mask64(n)) return;
+  // dup and fm serve only the reverse first fit of undecided vertices
+  const bool rff_left = __any_sync(kFull, (!dec[0] && lo[0] < hi[0]) || (!dec[1] && lo[1] < hi[1]));
+  const unsigned below = (1u << lane) - 1u;
+  // dup among the vertices colored by step P (undecided ones get unique keys)
+  if (rff_left) {
+    const int32_t k0 = dec[0] ? col[0] : -1 - lane, k1 = dec[1] ? col[1] : -1 - lane;
+    const unsigned m0 = __match_any_sync(kFull, k0), m1 = __match_any_sync(kFull, k1);
+    unsigned cross = 0u;  // first-half lanes with this lane's second color
+    for (int t = 0; t < 32; t++) {
+      const int32_t c = __shfl_sync(kFull, k0, t);
+      if (dec[1] && c == k1) cross |= 1u << t;
+    }
+    if (dec[0]) s_dup[lane] = m0 & below;
+    if (dec[1]) s_dup[lane + 32] = ((unsigned long long)(m1 & below) << 32) | cross;
+  }
+  // fm pushes of the colors decided by step P into the undecided reverse
+  // first-fit vertices, four loads in flight
+#pragma unroll
+  for (int h = 0; h < 2; h++) {
+    const int32_t v = lane + 32 * h;
+    unsigned long long todo = (!dec[h] && lo[h] < hi[h]) ? (adj[h] & decided0) : 0ull;
+    const uint32_t *lb = a.lbm + (slot0 + v) * a.words;
+    unsigned long long fm = 0ull;
+    while (todo) {
+      int32_t j[4], c[4];
+      uint32_t wd[4];
+#pragma unroll
+      for (int q = 0; q < 4; q++) {
+        j[q] = todo ? __ffsll((long long)todo) - 1 : -1;
+        todo &= todo - 1ull;
+        c[q] = j[q] >= 0 ? s_col[j[q]] : -1;
+        const bool in = j[q] >= 0 && c[q] > lo[h] && c[q] <= hi[h];
+        wd[q] = in ? lb[c[q] >> 5] : 0u;
+        if (!in) j[q] = -1;
+      }
+#pragma unroll
+      for (int q = 0; q < 4; q++)
+        if (j[q] >= 0 && ((wd[q] >> (c[q] & 31)) & 1u) == 0u) fm |= 1ull << j[q];
+    }
+    if (fm) s_fm[v] = fm;
+  }
+  __syncwarp();
+  for (int32_t i = 0; i < n; i++) {
+    if ((decided0 >> i) & 1ull) continue;
+    // fold the fm pushes of the previous step
+    if (rff_left) {
+#pragma unroll
+      for (int h = 0; h < 2; h++) {
+        if (pbit[h] >= 0 && ((pw[h] >> (pbit[h] & 31)) & 1u) == 0u)
+          s_fm[lane + 32 * h] |= 1ull << (pbit[h] >> 5);
+        pbit[h] = -1;
+      }
+      __syncwarp();
+    }
+    const int32_t li = i & 31, hv = i >> 5;
+    const unsigned long long am = s_adj[i];
+    bool in_o[2];
+#pragma unroll
+    for (int h = 0; h < 2; h++) in_o[h] = lane + 32 * h < i && ((am >> (lane + 32 * h)) & 1ull);
+    int32_t x = -1;
+    if (!((large >> i) & 1ull)) {
+      // small vertex: its window bitmap with the overlay ORed in (a copy)
+      const int32_t so = s_sown[i];
+      if (lane < kWords) wscr[lane] = s_bm[i][lane];
+      __syncwarp();
+#pragma unroll
+      for (int h = 0; h < 2; h++)
+        if (in_o[h] && col[h] < kSmallWindow) atomicOr(&wscr[col[h] >> 5], 1u << (col[h] & 31));
+      __syncwarp();
+      const uint32_t word = (lane < kWords) ? wscr[lane] : kFull;
+      if (so > a.T) x = win_kth_free_down(word, so - 1, s_k[i]);
+      if (x < 0) x = win_first_free_up(word, 0);
+      if (x < 0) {  // cannot happen within the window bounds
+        if (lane == 0) atomicOr(a.err, ERR_INTERNAL);
+        x = 0;
+      }
+      __syncwarp();
+    } else {
+      const int32_t rc = s_rcnt[i];
+      const int32_t *l = s_list[i];
+      if (rc == 0) {
+        // first fit: at most 63 neighbours take at most 63 of the 64 entries
+        const unsigned long long tk = pull_marks(l, kSumCand, in_o[0] ? col[0] : INT32_MIN,
+                                                 in_o[1] ? col[1] : INT32_MIN, pscr);
+        x = l[__ffsll((long long)~tk) - 1];
+      } else {
+        // reverse first fit: the window entries (colors <= ak, negated) that
+        // no neighbour takes, after skipping e of them
+        const int32_t ak = -l[0];
+        const unsigned long long tk =
+            pull_marks(l, rc, (in_o[0] && col[0] <= ak) ? -col[0] : INT32_MIN,
+                       (in_o[1] && col[1] <= ak) ? -col[1] : INT32_MIN, pscr);
+        const unsigned long long fmi = s_fm[i];
+        bool first[2];
+#pragma unroll
+        for (int h = 0; h < 2; h++)
+          first[h] = in_o[h] && ((fmi >> (lane + 32 * h)) & 1ull) &&
+                     (s_dup[lane + 32 * h] & am) == 0ull;
+        const int32_t e = __popc(__ballot_sync(kFull, first[0])) +
+                          __popc(__ballot_sync(kFull, first[1]));
+        const unsigned long long av = ~tk & low_mask64(rc);
+        if (__popcll(av) > e) {
+          x = -l[nth_set_bit64(av, e)];
+        } else if (rc == kSumCand) {
+          // e + (taken entries) <= |O| <= 63 < 64 entries
+          if (lane == 0) atomicOr(a.err, ERR_INTERNAL);
+          x = 0;
+        } else {
+          // no k-th free color: first fit over the 64 smallest free colors
+          const int32_t *rec = a.gsum + (slot0 + i) * kSumInts;
+          cx[lane] = rec[lane];
+          cx[lane + 32] = rec[32 + lane];
+          __syncwarp();
+          const unsigned long long tf = pull_marks(cx, kSumCand, in_o[0] ? col[0] : INT32_MIN,
+                                                   in_o[1] ? col[1] : INT32_MIN, pscr);
+          x = cx[__ffsll((long long)~tf) - 1];
+          __syncwarp();
+        }
+      }
+    }
+    // ---- i is decided: its duplicates, the later duplicates it leads, and
+    // the fm pushes of its color to the later vertices that test it
+    if (!rff_left) {
+      if (lane == li) {
+        col[hv] = x;
+        dec[hv] = true;
+      }
+      if (lane == 0) s_col[i] = x;
+      __syncwarp();
+      continue;
+    }
+    const unsigned long long dmask =
+        ((unsigned long long)__ballot_sync(kFull, dec[1] && lane + 32 < i && col[1] == x) << 32) |
+        __ballot_sync(kFull, dec[0] && lane < i && col[0] == x);
+#pragma unroll
+    for (int h = 0; h < 2; h++) {
+      const int32_t v = lane + 32 * h;
+      if (v == i) {
+        col[h] = x;
+        dec[h] = true;
+        s_dup[v] = dmask;
+      } else if (v > i && v < n) {
+        if (dec[h] && col[h] == x) s_dup[v] |= 1ull << i;
+        if (!dec[h] && ((adj[h] >> i) & 1ull) && x > lo[h] && x <= hi[h]) {
+          pw[h] = a.lbm[(slot0 + v) * a.words + (x >> 5)];
+          pbit[h] = (x & 31) | (i << 5);
+        }
+      }
+    }
+    if (lane == 0) s_col[i] = x;
+    __syncwarp();
+  }
+  __syncwarp();
 }
 
 template <int POLICY, int NT>
@@ -447,10 +677,14 @@ __global__ void __launch_bounds__(NT) k_color_wave(WaveArgs a) {
   __shared__ int32_t s_red[NW + 1];
   __shared__ int32_t s_state[4];  // col_max, col_next, npairs, stop
   constexpr int KC = (POLICY == BGPC_FF) ? kMaxChunk : 1;
-  __shared__ int32_t s_cand[KC][kCand];   // first-fit candidates of large vertices
-  __shared__ int32_t s_rcand[KC][kCand];  // reverse first-fit candidates (descending)
+  // first fit: each large vertex's candidate list (ascending; a reverse
+  // first-fit window is stored negated) and its window length (0: none)
+  __shared__ int32_t s_list[KC][kSumCand];
   __shared__ int32_t s_rcnt[KC];
+  __shared__ unsigned long long s_dup[KC], s_fm[KC];  // the walk's masks
+  __shared__ uint32_t s_pull[(POLICY == BGPC_FF) ? kPullBits / 32 : 1];  // the walk's scratch
   __shared__ int32_t s_cx[(POLICY == BGPC_FF) ? kSumCand : 1];  // a whole summary list
+  __shared__ uint32_t s_wscr[(POLICY == BGPC_FF) ? kWords : 1];   // a window with its overlay
   __shared__ unsigned long long s_large;
   extern __shared__ __align__(16) uint32_t s_big[];  // a.words: one large vertex's F
 
@@ -462,6 +696,8 @@ __global__ void __launch_bounds__(NT) k_color_wave(WaveArgs a) {
     return;
   }
   const bool small_ok = a.small_ok != 0;
+  if constexpr (POLICY == BGPC_FF)
+    for (int x = tid; x < kPullBits / 32; x += NT) s_pull[x] = 0u;  // kept zero by the walk
   const int32_t col_max0 = max(gm, 0);
 
   for (int32_t t = (int32_t)blockIdx.x; t < a.nchunks; t += (int32_t)gridDim.x) {
@@ -594,10 +830,13 @@ __global__ void __launch_bounds__(NT) k_color_wave(WaveArgs a) {
       for (int32_t iv = warp; iv < n; iv += NW) {
         if (!((large >> iv) & 1ull)) continue;
         const int32_t *rec = a.gsum + (slot0 + iv) * kSumInts;
-        s_cand[iv][lane] = rec[lane];
-        s_rcand[iv][lane] = rec[kSumCand + lane];
+        const int32_t f0 = rec[lane], f1 = rec[32 + lane];
+        const int32_t r0 = rec[kSumCand + lane], r1 = rec[kSumCand + 32 + lane];
+        const int32_t rc = (s_sown[iv] > a.T) ? rec[2 * kSumCand] : 0;
+        s_list[iv][lane] = rc > 0 ? -r0 : f0;
+        s_list[iv][lane + 32] = rc > 0 ? -r1 : f1;
         if (lane == 0) {
-          s_rcnt[iv] = rec[2 * kSumCand];
+          s_rcnt[iv] = rc;
           s_adj[iv] = *reinterpret_cast<const unsigned long long *>(rec + 2 * kSumCand + 2);
         }
       }
@@ -613,7 +852,7 @@ __global__ void __launch_bounds__(NT) k_color_wave(WaveArgs a) {
         int32_t x;
         const int32_t so = s_sown[iv];
         if ((large >> iv) & 1ull) {
-          x = (so > a.T && s_rcnt[iv] > 0) ? s_rcand[iv][0] : s_cand[iv][0];
+          x = (s_rcnt[iv] > 0) ? -s_list[iv][0] : s_list[iv][0];
         } else {
           const uint32_t word = (lane < kWords) ? s_bm[iv][lane] : kFull;
           x = (so > a.T) ? win_kth_free_down(word, so - 1, s_k[iv]) : -1;
@@ -628,23 +867,29 @@ __global__ void __launch_bounds__(NT) k_color_wave(WaveArgs a) {
       __syncthreads();
     }
 
-    // ---- phase B: resolve the chunk's vertices in order.  One warp walks the
-    // chunk (under first fit only the vertices with earlier neighbours are
-    // left); it stops only at a vertex that needs the whole CTA (a large
-    // vertex under B1/B2).
-    int32_t i = 0;
+    // ---- phase B (first fit): the vertices with earlier neighbours in the
+    // chunk, walked in order by one warp
+    if constexpr (POLICY == BGPC_FF) {
+      if (warp == 0)
+        ff_walk(a, n, slot0, large, s_adj, s_col, s_bm, s_sown, s_k, s_list, s_rcnt, s_dup, s_fm,
+                s_cx, s_wscr, s_pull);
+      __syncthreads();
+    }
+
+    // ---- phase B (B1, B2): resolve the chunk's vertices in order.  One warp
+    // walks the chunk; it stops only at a vertex that needs the whole CTA (a
+    // large vertex).
+    int32_t i = (POLICY == BGPC_FF) ? n : 0;
     while (i < n) {
       if (warp == 0) {
         int32_t col_max = s_state[0], col_next = s_state[1];
         int32_t ii = i;
         for (; ii < n; ii++) {
           const bool lg = (large >> ii) & 1ull;
-          if (lg && POLICY != BGPC_FF) break;
+          if (lg) break;
           const unsigned long long am = s_adj[ii];
           int32_t x = -1;
-          if (POLICY == BGPC_FF && am == 0ull) {
-            x = s_col[ii];  // step P
-          } else if (!lg) {
+          {
 #pragma unroll
             for (int h = 0; h < 2; h++) {
               const int32_t jj = lane + 32 * h;
@@ -676,83 +921,6 @@ __global__ void __launch_bounds__(NT) k_color_wave(WaveArgs a) {
               if (lane == 0) atomicOr(a.err, ERR_INTERNAL);
               x = 0;
             }
-          } else if constexpr (POLICY == BGPC_FF) {
-            // overlay colors, at most two per lane
-            int32_t oc[2];
-#pragma unroll
-            for (int h = 0; h < 2; h++) {
-              const int32_t jj = lane + 32 * h;
-              oc[h] = (jj < ii && ((am >> jj) & 1ull)) ? s_col[jj] : -1;
-            }
-            const int32_t *rec = a.gsum + (slot0 + ii) * kSumInts;
-            const int32_t so = s_sown[ii];
-            const int32_t rcnt = (so > a.T) ? s_rcnt[ii] : 0;
-            if (rcnt > 0) {
-              // k-th free color of F_S u O counted down from so - 1: skip the
-              // overlay colors that are free in F_S above the window, and the
-              // window entries that the overlay takes
-              const int32_t ak = s_rcand[ii][0];
-              const uint32_t *g = a.lbm + (slot0 + ii) * a.words;
-              // e = distinct overlay colors in (ak, so - 1] that are free in
-              // F_S (two chunk-mates may share a color: F is a set)
-              bool up[2];
-#pragma unroll
-              for (int h = 0; h < 2; h++) {
-                const int32_t c = oc[h];
-                up[h] = c > ak && c <= so - 1 && !((g[c >> 5] >> (c & 31)) & 1u);
-              }
-              const unsigned m0 = __match_any_sync(kFull, up[0] ? oc[0] : -1 - lane);
-              const unsigned m1 = __match_any_sync(kFull, up[1] ? oc[1] : -1 - lane);
-              bool first0 = up[0] && (__ffs(m0) - 1 == lane);
-              bool first1 = up[1] && (__ffs(m1) - 1 == lane);
-              if (__any_sync(kFull, first1)) {
-                for (int kk = 0; kk < 32; kk++) {
-                  const int32_t v0 = __shfl_sync(kFull, up[0] ? oc[0] : INT32_MIN, kk);
-                  if (first1 && v0 == oc[1]) first1 = false;
-                }
-              }
-              const int32_t e = __popc(__ballot_sync(kFull, first0)) +
-                                __popc(__ballot_sync(kFull, first1));
-              // the (e+1)-th window entry that no overlay color takes: first
-              // among the kCand entries kept here, else among all of them
-              const int32_t n1 = min(rcnt, kCand);
-              const int32_t *lst = s_rcand[ii];
-              unsigned long long av = ~overlay_marks(lst, n1, oc, ak, false) & low_mask64(n1);
-              if (__popcll(av) <= e && rcnt > kCand) {
-                s_cx[lane] = rec[kSumCand + lane];
-                s_cx[lane + 32] = rec[kSumCand + 32 + lane];
-                __syncwarp();
-                lst = s_cx;
-                av = ~overlay_marks(lst, rcnt, oc, ak, false) & low_mask64(rcnt);
-              }
-              if (__popcll(av) > e) {
-                for (int32_t t = 0; t < e; t++) av &= av - 1ull;  // drop the e lowest
-                x = lst[__ffsll((long long)av) - 1];
-              } else if (rcnt == kSumCand) {
-                // e + (taken entries) <= |O| <= 63 < 64 entries
-                if (lane == 0) atomicOr(a.err, ERR_INTERNAL);
-                x = 0;
-              }
-            }
-            if (x < 0) {
-              unsigned long long fr = ~overlay_marks(s_cand[ii], kCand, oc, INT32_MAX, true) &
-                                      low_mask64(kCand);
-              if (fr) {
-                x = s_cand[ii][__ffsll((long long)fr) - 1];
-              } else {
-                s_cx[lane] = rec[lane];
-                s_cx[lane + 32] = rec[32 + lane];
-                __syncwarp();
-                fr = ~overlay_marks(s_cx, kSumCand, oc, INT32_MAX, true);
-                if (fr) {
-                  x = s_cx[__ffsll((long long)fr) - 1];
-                } else {  // at most 63 overlay colors take at most 63 entries
-                  if (lane == 0) atomicOr(a.err, ERR_INTERNAL);
-                  x = 0;
-                }
-              }
-            }
-            __syncwarp();
           }
           col_max = max(col_max, x);
           if (POLICY == BGPC_B2) col_next = min(x + 1, col_max / 3 + 1);
@@ -768,11 +936,7 @@ __global__ void __launch_bounds__(NT) k_color_wave(WaveArgs a) {
       }
       __syncthreads();
       const int32_t L = s_state[3];
-      if (POLICY == BGPC_FF && L < n) {  // the first-fit walk never stops early
-        if (tid == 0) atomicOr(a.err, ERR_INTERNAL);
-        break;
-      }
-      if (POLICY != BGPC_FF && L < n) {
+      if (L < n) {
         // ---- CTA-wide path: the vertex's gathered forbidden set (k_gather)
         // in shared memory, searched with block-wide reductions (B1/B2 only:
         // first fit launches without the dynamic shared bitmap)
