@@ -397,6 +397,20 @@ __device__ __forceinline__ bool is_small(int32_t d2, int32_t deg, bool small_ok)
   return small_ok && d2 <= kSmallD2 && deg <= kSmallMaxDeg;
 }
 
+// A 4-byte asynchronous copy global -> shared (both 4-byte aligned), and the
+// per-thread group commit / wait around it.
+__device__ __forceinline__ void cp_async4(uint32_t *dst, const uint32_t *src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
 // Position of the set bit of v with n set bits below it (v has more than n).
 __device__ __forceinline__ int32_t nth_set_bit64(unsigned long long v, int32_t n) {
   int32_t pos = 0;
@@ -473,9 +487,11 @@ __device__ __forceinline__ unsigned long long pull_marks(const int32_t *l, int32
 // neighbour colors in (ak, so - 1] that are free in its forbidden set F_S
 // (reverse first fit: each shifts the k-th free color one further down).
 // Those F_S bits (fm, in shared memory) are pushed when a neighbour's color
-// is decided: the bitmap word is loaded then and folded in one step later, so
-// only the load for the immediately preceding vertex is waited for; dup
-// holds each vertex's earlier vertices of the same color (an overlay is a set).
+// is decided: the bitmap word is copied then (cp.async, into a landing slot
+// of the vertex, one per step parity) and folded in two walked steps later,
+// so a copy is waited for only by the vertex right after the one that
+// pushed it.  dup holds each vertex's earlier vertices of the same color (an
+// overlay is a set).
 __device__ __forceinline__ void ff_walk(const WaveArgs &a, int32_t n, int64_t slot0,
                                         unsigned long long large,
                                         const unsigned long long *s_adj, int32_t *s_col,
@@ -483,13 +499,14 @@ __device__ __forceinline__ void ff_walk(const WaveArgs &a, int32_t n, int64_t sl
                                         const int32_t *s_k, const int32_t (*s_list)[kSumCand],
                                         const int32_t *s_rcnt, unsigned long long *s_dup,
                                         unsigned long long *s_fm, int32_t *cx, uint32_t *wscr,
-                                        uint32_t *pscr) {
+                                        uint32_t *pscr, uint32_t *land) {
   const int lane = threadIdx.x & 31;
   unsigned long long adj[2];
   int32_t col[2], lo[2], hi[2];
   bool dec[2];
-  uint32_t pw[2];   // pending bitmap word of the last fm push
-  int32_t pbit[2];  // its bit (color & 31) and the pushing vertex: bit | j << 5, or -1
+  // pending fm pushes per step parity: bit (color & 31) | pushing vertex << 5,
+  // or -1; the word lands in land[parity][vertex]
+  int32_t pb[2][2];
 #pragma unroll
   for (int h = 0; h < 2; h++) {
     const int32_t v = lane + 32 * h;
@@ -501,8 +518,7 @@ __device__ __forceinline__ void ff_walk(const WaveArgs &a, int32_t n, int64_t sl
     lo[h] = rff ? -s_list[v][0] : INT32_MAX;  // fm tests colors in (lo, hi]
     hi[h] = rff ? s_sown[v] - 1 : INT32_MIN;
     if (valid) s_dup[v] = s_fm[v] = 0ull;
-    pw[h] = 0u;
-    pbit[h] = -1;
+    pb[0][h] = pb[1][h] = -1;
   }
   const unsigned long long decided0 =
       ((unsigned long long)__ballot_sync(kFull, dec[1]) << 32) | __ballot_sync(kFull, dec[0]);
@@ -549,15 +565,19 @@ __device__ __forceinline__ void ff_walk(const WaveArgs &a, int32_t n, int64_t sl
     if (fm) s_fm[v] = fm;
   }
   __syncwarp();
+  int32_t par = 0;  // parity of the walked step
   for (int32_t i = 0; i < n; i++) {
     if ((decided0 >> i) & 1ull) continue;
-    // fold the fm pushes of the previous step
+    // fold the fm pushes of two walked steps ago (their copies are done once
+    // at most the last step's group is pending)
     if (rff_left) {
+      cp_async_wait<1>();
 #pragma unroll
       for (int h = 0; h < 2; h++) {
-        if (pbit[h] >= 0 && ((pw[h] >> (pbit[h] & 31)) & 1u) == 0u)
-          s_fm[lane + 32 * h] |= 1ull << (pbit[h] >> 5);
-        pbit[h] = -1;
+        const int32_t b = par ? pb[1][h] : pb[0][h];
+        if (b >= 0 && ((land[par * kMaxChunk + lane + 32 * h] >> (b & 31)) & 1u) == 0u)
+          s_fm[lane + 32 * h] |= 1ull << (b >> 5);
+        if (par) pb[1][h] = -1; else pb[0][h] = -1;
       }
       __syncwarp();
     }
@@ -599,7 +619,17 @@ __device__ __forceinline__ void ff_walk(const WaveArgs &a, int32_t n, int64_t sl
         const unsigned long long tk =
             pull_marks(l, rc, (in_o[0] && col[0] <= ak) ? -col[0] : INT32_MIN,
                        (in_o[1] && col[1] <= ak) ? -col[1] : INT32_MIN, pscr);
-        const unsigned long long fmi = s_fm[i];
+        unsigned long long fmi = s_fm[i];
+        {  // the last walked step's push to i (its copy may be in flight)
+          int32_t pj = -1;
+          const int32_t b = par ? pb[0][hv] : pb[1][hv];
+          if (lane == li && b >= 0) {
+            cp_async_wait<0>();
+            if (((land[(par ^ 1) * kMaxChunk + i] >> (b & 31)) & 1u) == 0u) pj = b >> 5;
+          }
+          pj = __shfl_sync(kFull, pj, li);
+          if (pj >= 0) fmi |= 1ull << pj;
+        }
         bool first[2];
 #pragma unroll
         for (int h = 0; h < 2; h++)
@@ -651,14 +681,17 @@ __device__ __forceinline__ void ff_walk(const WaveArgs &a, int32_t n, int64_t sl
       } else if (v > i && v < n) {
         if (dec[h] && col[h] == x) s_dup[v] |= 1ull << i;
         if (!dec[h] && ((adj[h] >> i) & 1ull) && x > lo[h] && x <= hi[h]) {
-          pw[h] = a.lbm[(slot0 + v) * a.words + (x >> 5)];
-          pbit[h] = (x & 31) | (i << 5);
+          cp_async4(&land[par * kMaxChunk + v], a.lbm + (slot0 + v) * a.words + (x >> 5));
+          if (par) pb[1][h] = (x & 31) | (i << 5); else pb[0][h] = (x & 31) | (i << 5);
         }
       }
     }
+    cp_async_commit();
+    par ^= 1;
     if (lane == 0) s_col[i] = x;
     __syncwarp();
   }
+  cp_async_wait<0>();  // no copy into the landing slots outlives the chunk
   __syncwarp();
 }
 
@@ -682,6 +715,7 @@ __global__ void __launch_bounds__(NT) k_color_wave(WaveArgs a) {
   __shared__ int32_t s_list[KC][kSumCand];
   __shared__ int32_t s_rcnt[KC];
   __shared__ unsigned long long s_dup[KC], s_fm[KC];  // the walk's masks
+  __shared__ uint32_t s_land[2 * KC];                 // the walk's landing slots
   __shared__ uint32_t s_pull[(POLICY == BGPC_FF) ? kPullBits / 32 : 1];  // the walk's scratch
   __shared__ int32_t s_cx[(POLICY == BGPC_FF) ? kSumCand : 1];  // a whole summary list
   __shared__ uint32_t s_wscr[(POLICY == BGPC_FF) ? kWords : 1];   // a window with its overlay
@@ -872,7 +906,7 @@ __global__ void __launch_bounds__(NT) k_color_wave(WaveArgs a) {
     if constexpr (POLICY == BGPC_FF) {
       if (warp == 0)
         ff_walk(a, n, slot0, large, s_adj, s_col, s_bm, s_sown, s_k, s_list, s_rcnt, s_dup, s_fm,
-                s_cx, s_wscr, s_pull);
+                s_cx, s_wscr, s_pull, s_land);
       __syncthreads();
     }
 
