@@ -89,7 +89,8 @@ typedef struct {
     int32_t big_net;         /* T >= 0; default 64; INT32_MAX disables Alg. 8's rule */
     const int32_t *rank;     /* device, permutation of [0, n_a), or NULL for id order */
     int32_t max_rounds;      /* BGPC_EROUNDS beyond this; default 1000 */
-    int32_t validate;        /* 1: check sortedness, ranges, CSR/CSC agreement, rank */
+    int32_t validate;        /* 1: check sortedness, ranges, CSR/CSC agreement, rank
+                                (0: the graph is trusted as given) */
     int64_t stop_after_waves;/* debug: > 0 stops after that many waves (all rounds
                                 counted, empty waves too) and returns BGPC_STOPPED */
     int32_t *W_out;          /* debug, device [n_a] or NULL: work queue when stopped */

@@ -197,6 +197,7 @@ int color_impl(bgpc_ctx_t *ctx, const bgpc_graph_t &g, const bgpc_opts_t &o, int
   CU(grow(ctx->hub_net, (size_t)nnz / (kHubMin + 1) + 1));
   if (o.net_rounds > 0) CU(grow(ctx->netc, (size_t)n_a));
   CU(grow(ctx->ihub, nz));
+  CU(grow(ctx->brow, nz));
 
   // ---- setup (Alg. 1: W <- V_color, c <- -1), static graph analysis
   PhaseTimer tm(ctx, s, o.profile != 0);
@@ -209,8 +210,15 @@ int color_impl(bgpc_ctx_t *ctx, const bgpc_graph_t &g, const bgpc_opts_t &o, int
   // hub bitmaps: at most half the L2 cache in the first round
   nk += launch_hub_select(g.b_ptr, n_b, o.chunk, o.waves, (int64_t)ctx->l2_bytes / 8,
                           ctx->hub_id.p, ctx->hub_net.p, ctx->dev, sms, s);
-  nk += launch_tpos(g, ctx->tpos.p, &ctx->dev->err, ctx->hub_id.p,
-                    n_b > 0 ? ctx->ihub.p : nullptr, sms, s);
+  {
+    // the sort's scratch: buffers that are written only later in the setup
+    int32_t *const scratch[4] = {ctx->nc.p, ctx->npos.p, ctx->ihub.p, ctx->brow.p};
+    const int64_t hlen = tpos_hist_len(nnz);
+    CU(grow(ctx->thist, (size_t)(hlen > 0 ? hlen : 1)));
+    CU(grow(ctx->tsums, (size_t)(hlen / 4096 + 1)));
+    nk += launch_tpos(g, ctx->tpos.p, scratch, ctx->thist.p, ctx->tsums.p, o.validate,
+                      &ctx->dev->err, ctx->hub_id.p, n_b > 0 ? ctx->ihub.p : nullptr, sms, s);
+  }
   nk += launch_vertex_static(g, ctx->tpos.p, ctx->s_own.p, ctx->d2tot.p, ctx->nown.p,
                              o.net_rounds > 0 ? ctx->netc.p : nullptr, center_first, sms, s);
   nk += launch_init_queue(o.rank, n_a, ctx->W0.p, &ctx->dev->err, s);
@@ -882,7 +890,8 @@ int bgpc_ctx_destroy(bgpc_ctx_t *ctx) {
   release(ctx->tpos); release(ctx->nc); release(ctx->npos); release(ctx->nown);
   release(ctx->s_own); release(ctx->d2tot); release(ctx->W0); release(ctx->W1);
   release(ctx->kofs); release(ctx->stage); release(ctx->newpos); release(ctx->lose);
-  release(ctx->netc); release(ctx->ihub);
+  release(ctx->netc); release(ctx->ihub); release(ctx->brow);
+  release(ctx->thist); release(ctx->tsums);
   release(ctx->blocksum); release(ctx->bigt); release(ctx->bigd);
   release(ctx->hub_id); release(ctx->hub_net); release(ctx->nbm);
   release(ctx->cptr); release(ctx->cidx); release(ctx->dtab); release(ctx->vtab);

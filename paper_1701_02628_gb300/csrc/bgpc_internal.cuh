@@ -156,6 +156,8 @@ struct bgpc_ctx {
   bgpc::Buf<int32_t> s_own, d2tot, W0, W1, kofs, stage, newpos;
   bgpc::Buf<int32_t> netc;             // net-based first round: proposal of the owner net
   bgpc::Buf<int32_t> ihub;             // per CSR entry: hub slot of its net, or -1
+  bgpc::Buf<int32_t> brow;             // setup scratch (nnz ints)
+  bgpc::Buf<int32_t> thist, tsums;     // setup: digit counts of the tpos sort, scan scratch
   bgpc::Buf<uint8_t> lose;
   bgpc::Buf<int32_t> blocksum, bigt, bigd;
   bgpc::Buf<int32_t> wlist;            // chunks of the round ordered by wave
@@ -235,8 +237,15 @@ inline int div_up(long long a, long long b) { return (int)((a + b - 1) / b); }
 int launch_check_ptr(const int32_t *ptr, int32_t n, int32_t nnz, int32_t *err, cudaStream_t s);
 int launch_check_rows(const int32_t *ptr, const int32_t *idx, int32_t n, int32_t bound,
                        int32_t *err, int sms, cudaStream_t s);
-int launch_tpos(const bgpc_graph_t &g, int32_t *tpos, int32_t *err, const int32_t *hub_id,
+// tpos by a stable radix sort of the CSC indices by member id (scratch: four
+// arrays of nnz ints; hist: tpos_hist_len(nnz) ints; sums: its scan scratch);
+// validate: also check that CSR and CSC hold the same pairs.
+int64_t tpos_hist_len(int64_t nnz);
+int launch_tpos(const bgpc_graph_t &g, int32_t *tpos, int32_t *const scratch[4], int32_t *hist,
+                int32_t *sums, int32_t validate, int32_t *err, const int32_t *hub_id,
                 int32_t *ihub, int sms, cudaStream_t s);
+// Exclusive scan of a[0, len) in place (sums: ceil(len / 4096) scratch ints).
+int launch_excl_scan(int32_t *a, int64_t len, int32_t *sums, cudaStream_t s);
 int launch_vertex_static(const bgpc_graph_t &g, const int32_t *tpos, int32_t *s_own,
                           int32_t *d2tot, uint8_t *nown, int32_t *netc, int32_t center_first,
                           int sms, cudaStream_t s);

@@ -520,6 +520,16 @@ int adam_impl(bgpc_mlp_t *mlp, const float *grad, float lr, cudaStream_t s) {
 
 }  // namespace
 
+// Exclusive scan of a[0, len) in place (sums: ceil(len / 4096) scratch ints).
+int bgpc::launch_excl_scan(int32_t *a, int64_t len, int32_t *sums, cudaStream_t s) {
+  if (len <= 0) return 0;
+  const int32_t nsb = (int32_t)((len + kScanTile - 1) / kScanTile);
+  k_scan_tiles<<<nsb, kScanNT, 0, s>>>(a, len, sums);
+  k_scan_sums<<<1, kScanNT, 0, s>>>(sums, nsb);
+  k_scan_add<<<nsb, kScanNT, 0, s>>>(a, len, sums);
+  return 3;
+}
+
 extern "C" {
 
 int bgpc_features(bgpc_ctx_t *ctx, const bgpc_graph_t *g, int32_t big_net, float *X,

@@ -8,6 +8,7 @@ namespace bgpc {
 namespace {
 
 constexpr int kNT = 256;
+constexpr unsigned kFull = 0xffffffffu;
 
 __global__ void k_check_ptr(const int32_t *__restrict__ ptr, int32_t n, int32_t nnz,
                             int32_t *err) {
@@ -39,62 +40,112 @@ __global__ void k_check_rows(const int32_t *__restrict__ ptr, const int32_t *__r
   }
 }
 
-// tpos[i] = position of w inside vtxs(a_idx[i]) for CSR entry i of vertex w
-// (binary search in the sorted CSC column); a miss means CSR and CSC differ.
-// ihub[i] (when not NULL) = the hub slot of the net of CSR entry i, or -1.
-__global__ void k_tpos(const int32_t *__restrict__ a_ptr, const int32_t *__restrict__ a_idx,
-                       const int32_t *__restrict__ b_ptr, const int32_t *__restrict__ b_idx,
-                       int32_t n_a, int32_t *__restrict__ tpos, int32_t *err,
+// ---- tpos: the CSC entry of every CSR entry.  CSR entry i of vertex w is
+// the pair (w, v); the CSC lists each net's members in increasing order, so
+// the CSC indices f of w's pairs, in increasing f, are in increasing v: tpos
+// restricted to row w is exactly the CSC indices whose member is w, in
+// order.  tpos is therefore the stable sort of the CSC indices by member id
+// (an LSD radix sort, 8-bit digits, tiles of 4096 entries).
+constexpr int kSortPer = 16;
+constexpr int kSortTile = kNT * kSortPer;
+static_assert(kNT == 256, "one thread per digit");
+
+// Digit counts of one tile: hist[d * ntiles + tile].
+__global__ void __launch_bounds__(kNT) k_tsort_hist(const int32_t *__restrict__ key, int64_t n,
+                                                    int shift, int32_t ntiles,
+                                                    int32_t *__restrict__ hist) {
+  __shared__ int32_t cnt[256];
+  cnt[threadIdx.x] = 0;
+  __syncthreads();
+  const int64_t base = (int64_t)blockIdx.x * kSortTile + threadIdx.x;
+  int32_t d[kSortPer];
+#pragma unroll
+  for (int q = 0; q < kSortPer; q++) {
+    const int64_t i = base + (int64_t)q * kNT;
+    d[q] = i < n ? (int32_t)(((uint32_t)key[i] >> shift) & 255u) : -1;
+  }
+#pragma unroll
+  for (int q = 0; q < kSortPer; q++)
+    if (d[q] >= 0) atomicAdd(&cnt[d[q]], 1);
+  __syncthreads();
+  hist[(int64_t)threadIdx.x * ntiles + blockIdx.x] = cnt[threadIdx.x];
+}
+
+// Stable scatter of one tile, in 16 batches of 256: an entry goes to its
+// digit's start for this tile (scanned counts) plus the entries of that digit
+// in earlier batches, earlier warps and earlier lanes.  vin == nullptr: the
+// value is the index; kout == nullptr: keys are not written (last pass).
+__global__ void __launch_bounds__(kNT) k_tsort_scatter(const int32_t *__restrict__ kin,
+                                                       const int32_t *__restrict__ vin, int64_t n,
+                                                       int shift, int32_t ntiles,
+                                                       const int32_t *__restrict__ off,
+                                                       int32_t *__restrict__ kout,
+                                                       int32_t *__restrict__ vout) {
+  constexpr int NW = kNT / 32;
+  __shared__ int32_t wc[NW][256];
+  __shared__ int32_t run[256];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  run[threadIdx.x] = off[(int64_t)threadIdx.x * ntiles + blockIdx.x];
+  const int64_t base = (int64_t)blockIdx.x * kSortTile + threadIdx.x;
+  for (int q = 0; q < kSortPer; q++) {
+    for (int x = threadIdx.x; x < NW * 256; x += kNT) (&wc[0][0])[x] = 0;
+    __syncthreads();
+    const int64_t i = base + (int64_t)q * kNT;
+    const bool live = i < n;
+    int32_t k = 0, val = 0;
+    int d = -1 - lane;  // distinct dummies for lanes past the end
+    if (live) {
+      k = kin[i];
+      val = vin ? vin[i] : (int32_t)i;
+      d = (int)(((uint32_t)k >> shift) & 255u);
+    }
+    const unsigned peers = __match_any_sync(kFull, d);
+    const int before = __popc(peers & ((1u << lane) - 1u));
+    if (live && before == 0) wc[warp][d] = __popc(peers);
+    __syncthreads();
+    {  // this batch's start of each digit per warp, and the next batch's start
+      int32_t r = run[threadIdx.x];
+      for (int w = 0; w < NW; w++) {
+        const int32_t t = wc[w][threadIdx.x];
+        wc[w][threadIdx.x] = r;
+        r += t;
+      }
+      run[threadIdx.x] = r;
+    }
+    __syncthreads();
+    if (live) {
+      const int32_t pos = wc[warp][d] + before;
+      if (kout) kout[pos] = k;
+      vout[pos] = val;
+    }
+    __syncthreads();
+  }
+}
+
+// ihub[i] = the hub slot of the net of CSR entry i, or -1.
+__global__ void k_ihub(const int32_t *__restrict__ a_idx, int64_t nnz,
                        const int32_t *__restrict__ hub_id, int32_t *__restrict__ ihub) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nnz;
+       i += (int64_t)gridDim.x * blockDim.x)
+    ihub[i] = hub_id[a_idx[i]];
+}
+
+// Validation: CSR entry i = (w, v) and CSC entry tpos[i] are the same pair
+// (member w, in net v); otherwise CSR and CSC differ.
+__global__ void k_tpos_check(const int32_t *__restrict__ a_ptr, const int32_t *__restrict__ a_idx,
+                             const int32_t *__restrict__ b_ptr, const int32_t *__restrict__ b_idx,
+                             int32_t n_a, const int32_t *__restrict__ tpos, int32_t *err) {
   const int lane = threadIdx.x & 31;
   int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t w = warp; w < n_a; w += nwarps) {
-    int32_t beg = a_ptr[w], end = a_ptr[w + 1];
+    const int32_t beg = a_ptr[w], end = a_ptr[w + 1];
+    bool bad = false;
     for (int32_t i = beg + lane; i < end; i += 32) {
-      int32_t v = a_idx[i];
-      if (ihub) ihub[i] = hub_id[v];
-      int32_t lo = b_ptr[v], hi = b_ptr[v + 1];
-      // first index of vtxs(v) holding an id >= w: a few interpolation
-      // steps on the ids at the ends of the range (the members of a net are
-      // spread over the id space, so each step shrinks the range to about
-      // its square root), then bisection of what is left
-      if (hi - lo > 16) {
-        int32_t a0 = lo, a1 = hi - 1;  // the answer lies in [a0, a1 + 1]
-        int32_t v0 = b_idx[a0], v1 = b_idx[a1];
-        for (int it = 0; it < 6 && a1 - a0 > 16 && v0 < (int32_t)w && (int32_t)w <= v1; it++) {
-          int32_t g = a0 + (int32_t)((int64_t)(a1 - a0) * ((int64_t)w - v0) / ((int64_t)v1 - v0));
-          g = min(max(g, a0 + 1), a1 - 1);
-          const int32_t vg = b_idx[g];
-          if (vg < (int32_t)w) {
-            a0 = g;
-            v0 = vg;
-          } else {
-            a1 = g;
-            v1 = vg;
-          }
-        }
-        if ((int32_t)w <= v0) {
-          lo = a0;
-          hi = a0;
-        } else if ((int32_t)w > v1) {
-          lo = a1 + 1;
-          hi = a1 + 1;
-        } else {
-          lo = a0 + 1;  // b_idx[a0] < w <= b_idx[a1]
-          hi = a1;
-        }
-      }
-      while (lo < hi) {
-        int32_t mid = lo + ((hi - lo) >> 1);
-        if (b_idx[mid] < (int32_t)w) lo = mid + 1; else hi = mid;
-      }
-      if (lo >= b_ptr[v + 1] || b_idx[lo] != (int32_t)w) {
-        atomicOr(err, ERR_MISMATCH);
-        lo = b_ptr[v];  // keep the map in range
-      }
-      tpos[i] = lo;
+      const int32_t f = tpos[i], v = a_idx[i];
+      bad |= b_idx[f] != (int32_t)w || f < b_ptr[v] || f >= b_ptr[v + 1];
     }
+    if (__any_sync(kFull, bad) && lane == 0) atomicOr(err, ERR_MISMATCH);
   }
 }
 
@@ -149,7 +200,8 @@ __global__ void k_vertex_static(const int32_t *__restrict__ a_ptr,
       if (netc && mine) {
         int32_t k = f - b_ptr[own];
         if (center_first) k = ((int32_t)w == own) ? 0 : k + 1 - (own < (int32_t)w ? 1 : 0);
-        netc[w] = so - 1 - k;
+        // in [0, so) for consistent CSR and CSC (kept there for any input)
+        netc[w] = so - 1 - min(max(k, 0), max(so - 1, 0));
       }
     }
   }
@@ -266,12 +318,42 @@ int launch_check_rows(const int32_t *ptr, const int32_t *idx, int32_t n, int32_t
   return 1;
 }
 
-int launch_tpos(const bgpc_graph_t &g, int32_t *tpos, int32_t *err, const int32_t *hub_id,
+int64_t tpos_hist_len(int64_t nnz) { return div_up(nnz, (long long)kSortTile) * 256; }
+
+int launch_tpos(const bgpc_graph_t &g, int32_t *tpos, int32_t *const scratch[4], int32_t *hist,
+                int32_t *sums, int32_t validate, int32_t *err, const int32_t *hub_id,
                 int32_t *ihub, int sms, cudaStream_t s) {
-  if (g.n_a <= 0) return 0;
-  k_tpos<<<grid_warps(g.n_a, sms), kNT, 0, s>>>(g.a_ptr, g.a_idx, g.b_ptr, g.b_idx, g.n_a,
-                                                 tpos, err, hub_id, ihub);
-  return 1;
+  if (g.n_a <= 0 || g.nnz <= 0) return 0;
+  const int64_t n = g.nnz;
+  const int32_t ntiles = (int32_t)div_up(n, (long long)kSortTile);
+  const int64_t hlen = (int64_t)ntiles * 256;
+  const uint32_t top = g.n_a > 1 ? (uint32_t)(g.n_a - 1) : 1u;
+  const int passes = (32 - __builtin_clz(top) + 7) / 8;  // 8-bit digits of the member ids
+  int nk = 0;
+  const int32_t *kin = g.b_idx, *vin = nullptr;
+  for (int p = 0; p < passes; p++) {
+    const bool last = p == passes - 1;
+    int32_t *kout = last ? nullptr : scratch[2 * (p & 1)];
+    int32_t *vout = last ? tpos : scratch[2 * (p & 1) + 1];
+    k_tsort_hist<<<ntiles, kNT, 0, s>>>(kin, n, 8 * p, ntiles, hist);
+    nk += 1 + launch_excl_scan(hist, hlen, sums, s);
+    k_tsort_scatter<<<ntiles, kNT, 0, s>>>(kin, vin, n, 8 * p, ntiles, hist, kout, vout);
+    nk++;
+    kin = kout;
+    vin = vout;
+  }
+  if (validate) {
+    k_tpos_check<<<grid_warps(g.n_a, sms), kNT, 0, s>>>(g.a_ptr, g.a_idx, g.b_ptr, g.b_idx, g.n_a,
+                                                        tpos, err);
+    nk++;
+  }
+  if (ihub) {
+    long long grid = div_up(n, (long long)kNT);
+    if (grid > (long long)sms * 16) grid = (long long)sms * 16;
+    k_ihub<<<(int)grid, kNT, 0, s>>>(g.a_idx, n, hub_id, ihub);
+    nk++;
+  }
+  return nk;
 }
 
 int launch_vertex_static(const bgpc_graph_t &g, const int32_t *tpos, int32_t *s_own,

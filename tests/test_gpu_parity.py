@@ -274,6 +274,19 @@ def test_errors(bg, ctx):
     with pytest.raises(bg.BgpcError) as e:
         bg.bgpc_color(ctx, bad, validate=True)
     assert e.value.status == bg.BGPC_EUNSORTED
+    # CSR and CSC each sorted and in range but holding different pairs (one
+    # member of a net swapped for a vertex outside it, in both directions of
+    # the row order): the validation's pair check
+    v = int(np.argmax(np.diff(g.b_ptr)))
+    members = set(g.b_idx[g.b_ptr[v]:g.b_ptr[v + 1]].tolist())
+    w_out = next(u for u in range(g.n_a) if u not in members)
+    lst = sorted((members - {int(g.b_idx[g.b_ptr[v]])}) | {w_out})
+    b_idx = dg.b_idx.clone()
+    b_idx[g.b_ptr[v]:g.b_ptr[v + 1]] = torch.as_tensor(lst, dtype=torch.int32, device="cuda:0")
+    bad = bg.DeviceGraph(dg.n_a, dg.n_b, dg.a_ptr, dg.a_idx, dg.b_ptr, b_idx)
+    with pytest.raises(bg.BgpcError) as e:
+        bg.bgpc_color(ctx, bad, validate=True)
+    assert e.value.status == bg.BGPC_EUNSORTED
     # index out of range
     a_idx = dg.a_idx.clone()
     a_idx[g.a_ptr[1] - 1] = g.n_b + 5
