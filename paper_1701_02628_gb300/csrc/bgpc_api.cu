@@ -415,9 +415,10 @@ int color_impl(bgpc_ctx_t *ctx, const bgpc_graph_t &g, const bgpc_opts_t &o, int
         nk++;
         st.color_launches++;
         ev = tm.begin();
-        nk += launch_publish(g.a_ptr, nhub > 0 ? ctx->ihub.p : nullptr, ctx->tpos.p, W,
-                             ctx->stage.p, wchunks, nwave, C, m, ctx->nc.p, colors, ctx->nbm.p,
-                             words, ctx->dev, sms, s);
+        nk += launch_publish(g.a_ptr, ctx->d2tot.p, nhub > 0 ? ctx->ihub.p : nullptr,
+                             ctx->tpos.p, W, ctx->stage.p, ctx->wlist.p, C, m, small_ok,
+                             ga.slot_lo, ga.slot_hi, ctx->segoff.p, ctx->segmap.p, ctx->nc.p,
+                             colors, ctx->nbm.p, words, ctx->dev, sms, s);
         tm.end(ev, PH_PUBLISH);
       }
       waves_done++;

@@ -1713,24 +1713,31 @@ __global__ void __launch_bounds__(kScanNT) k_piece_scatter(int32_t nslots,
 // Publish: colors of the wave's positions go to c[] and to every CSC entry
 // of their edges (nc), and the running max color is updated.  ihub[i] is the
 // hub slot of CSR entry i's net (-1: not a hub), read in CSR order instead of
-// looking the net up at random.
-__global__ void k_publish(const int32_t *__restrict__ a_ptr, const int32_t *__restrict__ ihub,
-                          const int32_t *__restrict__ tpos,
+// looking the net up at random.  Large vertices are published piece by piece
+// from the wave's piece map (one warp per piece of up to 32 nets, one lane
+// per incidence; every piece also writes the vertex's color), so a vertex of
+// thousands of nets is spread over many warps; small vertices (at most 16
+// nets, no pieces) take half a warp each.
+__global__ void k_publish(const int32_t *__restrict__ a_ptr, const int32_t *__restrict__ d2tot,
+                          const int32_t *__restrict__ ihub, const int32_t *__restrict__ tpos,
                           const int32_t *__restrict__ W, const int32_t *__restrict__ stage,
-                          const int32_t *__restrict__ chunks, int32_t nchunks, int32_t C,
-                          int32_t m, int32_t *__restrict__ nc, int32_t *__restrict__ colors,
+                          const int32_t *__restrict__ wlist, int32_t C, int32_t m,
+                          int32_t small_ok, int32_t slot_lo, int32_t slot_hi,
+                          const int32_t *__restrict__ segoff, const int4 *__restrict__ segmap,
+                          int32_t *__restrict__ nc, int32_t *__restrict__ colors,
                           uint32_t *__restrict__ nbm, int32_t words, DevScalars *dev) {
   const int lane = threadIdx.x & 31;
-  int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   int32_t mx = -1;
-  const int64_t total = (int64_t)nchunks * C;
-  for (int64_t t = warp; t < total; t += nwarps) {
-    const int64_t p = (int64_t)chunks[t / C] * C + t % C;
-    if (p >= m) continue;
-    const int32_t w = W[p], col = stage[p];
-    const int32_t beg = a_ptr[w], end = a_ptr[w + 1];
-    for (int32_t i = beg + lane; i < end; i += 32) {
+  // large vertices: their pieces
+  const int32_t sbeg = segoff[slot_lo], send = segoff[slot_hi];
+  for (int64_t sg = sbeg + warp; sg < send; sg += nwarps) {
+    const int4 sm = segmap[sg];
+    const int32_t u = sm.x, w = sm.y, ib = sm.z, nn = sm.w & 63;
+    const int32_t col = stage[wlist[u / C] * C + u % C];
+    if (lane < nn) {
+      const int32_t i = ib + lane;
       nc[tpos[i]] = col;
       if (ihub) {  // the color joins the bitmap of every hub net of w
         const int32_t h = ihub[i];
@@ -1739,6 +1746,28 @@ __global__ void k_publish(const int32_t *__restrict__ a_ptr, const int32_t *__re
     }
     if (lane == 0) colors[w] = col;
     mx = max(mx, col);
+  }
+  // small vertices: half a warp each
+  if (small_ok) {
+    const int32_t hl = lane & 15;
+    for (int64_t u = (int64_t)slot_lo + 2 * warp + (lane >> 4); u < slot_hi; u += 2 * nwarps) {
+      const int64_t p = (int64_t)wlist[u / C] * C + u % C;
+      if (p >= m) continue;
+      const int32_t w = W[p];
+      const int32_t beg = a_ptr[w], deg = a_ptr[w + 1] - beg;
+      if (!is_small(d2tot[w], deg, true)) continue;
+      const int32_t col = stage[p];
+      if (hl < deg) {
+        const int32_t i = beg + hl;
+        nc[tpos[i]] = col;
+        if (ihub) {
+          const int32_t h = ihub[i];
+          if (h >= 0) atomicOr(&nbm[(int64_t)h * words + (col >> 5)], 1u << (col & 31));
+        }
+      }
+      if (hl == 0) colors[w] = col;
+      mx = max(mx, col);
+    }
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(kFull, mx, o));
@@ -1852,17 +1881,20 @@ int launch_pieces(const int32_t *a_ptr, const int32_t *d2tot, const int32_t *W,
   return 3;
 }
 
-int launch_publish(const int32_t *a_ptr, const int32_t *ihub, const int32_t *tpos,
-                   const int32_t *W, const int32_t *stage, const int32_t *chunks,
-                   int32_t nchunks, int32_t C, int32_t m, int32_t *nc, int32_t *colors,
-                   uint32_t *nbm, int32_t words, DevScalars *dev, int sms, cudaStream_t s) {
-  if (nchunks <= 0) return 0;
-  long long warps = (long long)nchunks * C;
-  long long grid = div_up(warps * 32, 256);
-  // one resident set (8 CTAs of 256 per SM): no late second set as a tail
+int launch_publish(const int32_t *a_ptr, const int32_t *d2tot, const int32_t *ihub,
+                   const int32_t *tpos, const int32_t *W, const int32_t *stage,
+                   const int32_t *wlist, int32_t C, int32_t m, int32_t small_ok,
+                   int32_t slot_lo, int32_t slot_hi, const int32_t *segoff, const int4 *segmap,
+                   int32_t *nc, int32_t *colors, uint32_t *nbm, int32_t words, DevScalars *dev,
+                   int sms, cudaStream_t s) {
+  if (slot_hi <= slot_lo) return 0;
+  // one resident set (8 CTAs of 256 per SM), grid-stride over pieces and slots
+  long long grid = div_up((long long)(slot_hi - slot_lo) * 32, 256);
   if (grid > (long long)sms * 8) grid = (long long)sms * 8;
-  k_publish<<<(int)grid, 256, 0, s>>>(a_ptr, ihub, tpos, W, stage, chunks, nchunks, C, m, nc,
-                                      colors, nbm, words, dev);
+  if (grid < 1) grid = 1;
+  k_publish<<<(int)grid, 256, 0, s>>>(a_ptr, d2tot, ihub, tpos, W, stage, wlist, C, m, small_ok,
+                                      slot_lo, slot_hi, segoff, segmap, nc, colors, nbm, words,
+                                      dev);
   return 1;
 }
 

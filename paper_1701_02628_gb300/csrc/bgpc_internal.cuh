@@ -320,10 +320,12 @@ int launch_pieces(const int32_t *a_ptr, const int32_t *d2tot, const int32_t *W,
                   const int32_t *wlist, int32_t nch, int32_t C, int32_t m, int32_t small_ok,
                   int32_t *segoff, int32_t *blocksum, int4 *segmap, DevScalars *dev,
                   cudaStream_t s);
-int launch_publish(const int32_t *a_ptr, const int32_t *ihub, const int32_t *tpos,
-                   const int32_t *W, const int32_t *stage, const int32_t *chunks,
-                   int32_t nchunks, int32_t C, int32_t m, int32_t *nc, int32_t *colors,
-                   uint32_t *nbm, int32_t words, DevScalars *dev, int sms, cudaStream_t s);
+int launch_publish(const int32_t *a_ptr, const int32_t *d2tot, const int32_t *ihub,
+                   const int32_t *tpos, const int32_t *W, const int32_t *stage,
+                   const int32_t *wlist, int32_t C, int32_t m, int32_t small_ok,
+                   int32_t slot_lo, int32_t slot_hi, const int32_t *segoff, const int4 *segmap,
+                   int32_t *nc, int32_t *colors, uint32_t *nbm, int32_t words, DevScalars *dev,
+                   int sms, cudaStream_t s);
 // Per round: hub nets (more than H members) get a slot (hub_id, -1 otherwise)
 // and a color bitmap of their published members.
 int launch_hub_select(const int32_t *b_ptr, int32_t n_b, int32_t C, int32_t Q,
