@@ -181,6 +181,9 @@ int color_impl(bgpc_ctx_t *ctx, const bgpc_graph_t &g, const bgpc_opts_t &o, int
   CU(grow(ctx->npos, nz));
   CU(grow(ctx->nown, nz));
   CU(grow(ctx->s_own, (size_t)n_a));
+  CU(grow(ctx->ownid, (size_t)n_a));
+  for (int q = 0; q < 4; q++) CU(grow(ctx->ksc[q], (size_t)n_a));
+  CU(grow(ctx->kgstart, (size_t)(n_b > 0 ? n_b : 1)));
   CU(grow(ctx->d2tot, (size_t)n_a));
   CU(grow(ctx->W0, (size_t)n_a));
   CU(grow(ctx->W1, (size_t)n_a));
@@ -220,7 +223,8 @@ int color_impl(bgpc_ctx_t *ctx, const bgpc_graph_t &g, const bgpc_opts_t &o, int
                       &ctx->dev->err, ctx->hub_id.p, n_b > 0 ? ctx->ihub.p : nullptr, sms, s);
   }
   nk += launch_vertex_static(g, ctx->tpos.p, ctx->s_own.p, ctx->d2tot.p, ctx->nown.p,
-                             o.net_rounds > 0 ? ctx->netc.p : nullptr, center_first, sms, s);
+                             o.net_rounds > 0 ? ctx->netc.p : nullptr, center_first,
+                             ctx->ownid.p, sms, s);
   nk += launch_init_queue(o.rank, n_a, ctx->W0.p, &ctx->dev->err, s);
   nk += launch_init_mirror(g, o.rank, ctx->nc.p, ctx->npos.p, colors, sms, s);
   tm.end(ev, PH_SETUP);
@@ -279,9 +283,18 @@ int color_impl(bgpc_ctx_t *ctx, const bgpc_graph_t &g, const bgpc_opts_t &o, int
       waves_done++;
     } else {
     ev = tm.begin();
-    if (nbig_t > 0)
+    if (nbig_t > 0 && !o.rank) {
+      // W in id order: k by a sort of the W positions by owner net (work in |W|)
+      int32_t *const sc[4] = {ctx->ksc[0].p, ctx->ksc[1].p, ctx->ksc[2].p, ctx->ksc[3].p};
+      const int64_t hlen = tpos_hist_len(m);
+      CU(grow(ctx->thist, (size_t)(hlen > 0 ? hlen : 1)));
+      CU(grow(ctx->tsums, (size_t)(hlen / 4096 + 1)));
+      nk += launch_kofs_sorted(W, m, ctx->ownid.p, ctx->s_own.p, o.big_net, n_b, sc,
+                               ctx->thist.p, ctx->tsums.p, ctx->kgstart.p, ctx->kofs.p, sms, s);
+    } else if (nbig_t > 0) {
       nk += launch_kofs(g.b_ptr, ctx->nc.p, ctx->npos.p, ctx->nown.p, ctx->bigt.p, nbig_t,
                         ctx->kofs.p, sms, s);
+    }
     CU(cudaMemsetAsync(&ctx->dev->trav, 0, kRoundCounters * sizeof(unsigned long long), s));
     nk += launch_trav(g.a_ptr, W, ctx->d2tot.p, m, small_ok, ctx->dev, s);
     tm.end(ev, PH_DETECT);
@@ -892,7 +905,8 @@ int bgpc_ctx_destroy(bgpc_ctx_t *ctx) {
   release(ctx->s_own); release(ctx->d2tot); release(ctx->W0); release(ctx->W1);
   release(ctx->kofs); release(ctx->stage); release(ctx->newpos); release(ctx->lose);
   release(ctx->netc); release(ctx->ihub); release(ctx->brow);
-  release(ctx->thist); release(ctx->tsums);
+  release(ctx->thist); release(ctx->tsums); release(ctx->ownid); release(ctx->kgstart);
+  for (int q = 0; q < 4; q++) release(ctx->ksc[q]);
   release(ctx->blocksum); release(ctx->bigt); release(ctx->bigd);
   release(ctx->hub_id); release(ctx->hub_net); release(ctx->nbm);
   release(ctx->cptr); release(ctx->cidx); release(ctx->dtab); release(ctx->vtab);

@@ -158,6 +158,8 @@ struct bgpc_ctx {
   bgpc::Buf<int32_t> ihub;             // per CSR entry: hub slot of its net, or -1
   bgpc::Buf<int32_t> brow;             // setup scratch (nnz ints)
   bgpc::Buf<int32_t> thist, tsums;     // setup: digit counts of the tpos sort, scan scratch
+  bgpc::Buf<int32_t> ownid;            // owner net of each vertex (-1: none)
+  bgpc::Buf<int32_t> ksc[4], kgstart;  // kofs sort: scratch [n_a] x 4, group starts [n_b]
   bgpc::Buf<uint8_t> lose;
   bgpc::Buf<int32_t> blocksum, bigt, bigd;
   bgpc::Buf<int32_t> wlist;            // chunks of the round ordered by wave
@@ -248,7 +250,12 @@ int launch_tpos(const bgpc_graph_t &g, int32_t *tpos, int32_t *const scratch[4],
 int launch_excl_scan(int32_t *a, int64_t len, int32_t *sums, cudaStream_t s);
 int launch_vertex_static(const bgpc_graph_t &g, const int32_t *tpos, int32_t *s_own,
                           int32_t *d2tot, uint8_t *nown, int32_t *netc, int32_t center_first,
-                          int sms, cudaStream_t s);
+                          int32_t *ownid, int sms, cudaStream_t s);
+// kofs for W in id order, by a stable sort of the W positions by owner net
+// (scratch: four arrays of m ints; hist: tpos_hist_len(m); gstart: n_b ints)
+int launch_kofs_sorted(const int32_t *W, int32_t m, const int32_t *ownid, const int32_t *s_own,
+                       int32_t T, int32_t n_b, int32_t *const scratch[4], int32_t *hist,
+                       int32_t *sums, int32_t *gstart, int32_t *kofs, int sms, cudaStream_t s);
 // The net-based first round (Alg. 8 / Alg. 9): its colors, computed by
 // launch_vertex_static into netc, published into c and the mirror.
 int launch_net_publish(const bgpc_graph_t &g, const int32_t *netc, const int32_t *rank,

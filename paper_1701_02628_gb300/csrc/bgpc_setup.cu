@@ -130,6 +130,40 @@ __global__ void k_ihub(const int32_t *__restrict__ a_idx, int64_t nnz,
     ihub[i] = hub_id[a_idx[i]];
 }
 
+// ---- kofs in id order (W in increasing id): a vertex's k is the number of
+// earlier W vertices with the same owner net (of more than T members), i.e.
+// its index within its owner's group after a stable sort of the W positions
+// by owner net.  Keys: the owner net, or n_b for the vertices without one.
+__global__ void k_kofs_keys(const int32_t *__restrict__ W, int32_t m,
+                            const int32_t *__restrict__ ownid, const int32_t *__restrict__ s_own,
+                            int32_t T, int32_t n_b, int32_t *__restrict__ key) {
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < m;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t w = W[p];
+    key[p] = s_own[w] > T ? ownid[w] : n_b;
+  }
+}
+
+// gstart[v] = the first sorted index of group v.
+__global__ void k_kofs_heads(const int32_t *__restrict__ ks, int32_t m, int32_t n_b,
+                             int32_t *__restrict__ gstart) {
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < m;
+       j += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t k = ks[j];
+    if (k < n_b && (j == 0 || ks[j - 1] != k)) gstart[k] = (int32_t)j;
+  }
+}
+
+__global__ void k_kofs_write(const int32_t *__restrict__ ks, const int32_t *__restrict__ vs,
+                             int32_t m, int32_t n_b, const int32_t *__restrict__ gstart,
+                             int32_t *__restrict__ kofs) {
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < m;
+       j += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t k = ks[j];
+    if (k < n_b) kofs[vs[j]] = (int32_t)j - gstart[k];
+  }
+}
+
 // Validation: CSR entry i = (w, v) and CSC entry tpos[i] are the same pair
 // (member w, in net v); otherwise CSR and CSC differ.
 __global__ void k_tpos_check(const int32_t *__restrict__ a_ptr, const int32_t *__restrict__ a_idx,
@@ -165,7 +199,7 @@ __global__ void k_vertex_static(const int32_t *__restrict__ a_ptr,
                                 const int32_t *__restrict__ tpos, int32_t n_a,
                                 int32_t *__restrict__ s_own, int32_t *__restrict__ d2tot,
                                 uint8_t *__restrict__ nown, int32_t *__restrict__ netc,
-                                int32_t center_first) {
+                                int32_t center_first, int32_t *__restrict__ ownid) {
   const int lane = threadIdx.x & 31;
   int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -190,6 +224,7 @@ __global__ void k_vertex_static(const int32_t *__restrict__ a_ptr,
     const int32_t so = (end > beg) ? (int32_t)(best >> 32) : 0;
     if (lane == 0) {
       s_own[w] = so;
+      ownid[w] = own;
       d2tot[w] = (int32_t)sum;
       if (netc && end == beg) netc[w] = -1;
     }
@@ -356,13 +391,42 @@ int launch_tpos(const bgpc_graph_t &g, int32_t *tpos, int32_t *const scratch[4],
   return nk;
 }
 
+int launch_kofs_sorted(const int32_t *W, int32_t m, const int32_t *ownid, const int32_t *s_own,
+                       int32_t T, int32_t n_b, int32_t *const scratch[4], int32_t *hist,
+                       int32_t *sums, int32_t *gstart, int32_t *kofs, int sms, cudaStream_t s) {
+  if (m <= 0) return 0;
+  const int32_t ntiles = (int32_t)div_up((long long)m, (long long)kSortTile);
+  const int64_t hlen = (int64_t)ntiles * 256;
+  long long grid = div_up((long long)m, (long long)kNT);
+  if (grid > (long long)sms * 16) grid = (long long)sms * 16;
+  int nk = 0;
+  k_kofs_keys<<<(int)grid, kNT, 0, s>>>(W, m, ownid, s_own, T, n_b, scratch[0]);
+  nk++;
+  const int passes = (32 - __builtin_clz((uint32_t)(n_b > 0 ? n_b : 1)) + 7) / 8;
+  // pass p reads the pair (p & 1) (pass 0: the keys alone) and writes the other
+  const int32_t *kin = scratch[0], *vin = nullptr;
+  for (int p = 0; p < passes; p++) {
+    int32_t *kout = scratch[2 * ((p + 1) & 1)];
+    int32_t *vout = scratch[2 * ((p + 1) & 1) + 1];
+    k_tsort_hist<<<ntiles, kNT, 0, s>>>(kin, m, 8 * p, ntiles, hist);
+    nk += 1 + launch_excl_scan(hist, hlen, sums, s);
+    k_tsort_scatter<<<ntiles, kNT, 0, s>>>(kin, vin, m, 8 * p, ntiles, hist, kout, vout);
+    nk++;
+    kin = kout;
+    vin = vout;
+  }
+  k_kofs_heads<<<(int)grid, kNT, 0, s>>>(kin, m, n_b, gstart);
+  k_kofs_write<<<(int)grid, kNT, 0, s>>>(kin, vin, m, n_b, gstart, kofs);
+  return nk + 2;
+}
+
 int launch_vertex_static(const bgpc_graph_t &g, const int32_t *tpos, int32_t *s_own,
                           int32_t *d2tot, uint8_t *nown, int32_t *netc, int32_t center_first,
-                          int sms, cudaStream_t s) {
+                          int32_t *ownid, int sms, cudaStream_t s) {
   if (g.n_a <= 0) return 0;
   k_vertex_static<<<grid_warps(g.n_a, sms), kNT, 0, s>>>(g.a_ptr, g.a_idx, g.b_ptr, tpos,
                                                           g.n_a, s_own, d2tot, nown, netc,
-                                                          center_first);
+                                                          center_first, ownid);
   return 1;
 }
 
