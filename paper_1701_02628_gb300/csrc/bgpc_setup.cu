@@ -87,18 +87,22 @@ __global__ void __launch_bounds__(kNT) k_tsort_scatter(const int32_t *__restrict
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   run[threadIdx.x] = off[(int64_t)threadIdx.x * ntiles + blockIdx.x];
   const int64_t base = (int64_t)blockIdx.x * kSortTile + threadIdx.x;
+  // the tile's keys and values, all loaded before the batches are ranked
+  int32_t kq[kSortPer], vq[kSortPer];
+#pragma unroll
+  for (int q = 0; q < kSortPer; q++) {
+    const int64_t i = base + (int64_t)q * kNT;
+    kq[q] = i < n ? kin[i] : 0;
+    vq[q] = i < n ? (vin ? vin[i] : (int32_t)i) : 0;
+  }
+#pragma unroll
   for (int q = 0; q < kSortPer; q++) {
     for (int x = threadIdx.x; x < NW * 256; x += kNT) (&wc[0][0])[x] = 0;
     __syncthreads();
     const int64_t i = base + (int64_t)q * kNT;
     const bool live = i < n;
-    int32_t k = 0, val = 0;
-    int d = -1 - lane;  // distinct dummies for lanes past the end
-    if (live) {
-      k = kin[i];
-      val = vin ? vin[i] : (int32_t)i;
-      d = (int)(((uint32_t)k >> shift) & 255u);
-    }
+    const int32_t k = kq[q], val = vq[q];
+    const int d = live ? (int)(((uint32_t)k >> shift) & 255u) : -1 - lane;  // dummies differ
     const unsigned peers = __match_any_sync(kFull, d);
     const int before = __popc(peers & ((1u << lane) - 1u));
     if (live && before == 0) wc[warp][d] = __popc(peers);
