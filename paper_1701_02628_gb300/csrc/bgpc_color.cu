@@ -411,6 +411,26 @@ __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
+// A chunk whose earlier vertices spread over more ids than this tests its
+// hub chunk-mates pair by pair instead of reading the hubs' member windows.
+constexpr int32_t kHubScanSpan = 2048;
+
+// Position of the set bit of v with n set bits below it (v has more than n;
+// 0 when it has not).
+__device__ __forceinline__ int32_t nth_set_bit32(uint32_t v, int32_t n) {
+  int32_t pos = 0;
+#pragma unroll
+  for (int w = 16; w > 0; w >>= 1) {
+    const int32_t c = __popc(v & ((1u << w) - 1u));
+    if (n >= c) {
+      n -= c;
+      v >>= w;
+      pos += w;
+    }
+  }
+  return pos & 31;
+}
+
 // Position of the set bit of v with n set bits below it (v has more than n).
 __device__ __forceinline__ int32_t nth_set_bit64(unsigned long long v, int32_t n) {
   int32_t pos = 0;
@@ -1417,12 +1437,12 @@ __global__ void __launch_bounds__(NT, 4) k_gather_w(GatherArgs a) {
       so = a.s_own[w];
       qor = min(W4, max(so > a.T ? ((so - 1) >> 7) + 1 : 0, 2));
     }
-    int32_t sz = 0, bp = 0, hub = -1, tp = 0;
+    int32_t sz = 0, bp = 0, hub = -1, tp = 0, vnet = 0;
     if (lane < nnets) {
-      const int32_t v = a.a_idx[ibeg + lane];
-      bp = a.b_ptr[v];
-      sz = a.b_ptr[v + 1] - bp;
-      hub = a.hub_id ? a.hub_id[v] : -1;
+      vnet = a.a_idx[ibeg + lane];
+      bp = a.b_ptr[vnet];
+      sz = a.b_ptr[vnet + 1] - bp;
+      hub = a.hub_id ? a.hub_id[vnet] : -1;
       if (a.id_order && hub >= 0) tp = a.tpos[ibeg + lane];
     }
     const unsigned hubs = __ballot_sync(kFull, hub >= 0);
@@ -1431,20 +1451,40 @@ __global__ void __launch_bounds__(NT, 4) k_gather_w(GatherArgs a) {
       n_trav_hub += (unsigned long long)__reduce_add_sync(kFull, hub >= 0 ? sz - 1 : 0);
       n_hub_pairs += (unsigned long long)__popc(hubs);
       n_hub_groups += (unsigned long long)__popc(hubs) * qor;
-      int32_t id_lo = 0, id_hi = 0;
-      if (a.id_order && rel_hi > 0) {
-        id_lo = a.W[p0];
-        id_hi = a.W[p0 + rel_hi - 1];
-      }
+      const int32_t id_lo = (a.id_order && rel_hi > 0) ? a.W[p0] : 0;
       warp_hub_or(s_bm4, nb4, W4, hubs, hub, 0, qor);
-      // their earlier chunk-mates.  In id order a chunk's earlier vertices
-      // have ids in [id_lo, w), so in the id-sorted vtxs(v) they sit right
-      // before w's own entry (its CSC index tp): read backwards from there
-      // while the ids stay >= id_lo (one window of 32 per step, usually one
-      // step); the mirror words of those entries carry the queue positions.
-      // Four hubs per step: their first windows (ids and mirror words) are
-      // loaded together.
-      for (unsigned hm = hubs; hm && rel_hi > 0 && a.id_order;) {
+      // their earlier chunk-mates.  A chunk whose ids spread wide (later
+      // rounds, or a caller's rank order): every (hub, earlier chunk-mate)
+      // pair is tested directly, one per lane, by bisecting the hub's net id
+      // in the chunk-mate's sorted net list (short and contiguous).
+      const bool wide = rel_hi > 0 && (!a.id_order || w - id_lo > kHubScanSpan);
+      if (wide) {
+        const int32_t npairs = __popc(hubs) * rel_hi;
+        for (int32_t q0 = 0; q0 < npairs; q0 += 32) {
+          const int32_t q = q0 + lane;
+          const int32_t k = q < npairs ? q / rel_hi : 0, j = q - k * rel_hi;
+          const int32_t hv = __shfl_sync(kFull, vnet, nth_set_bit32(hubs, k));
+          if (q < npairs) {
+            const int32_t u = a.W[p0 + j];
+            int32_t lo = a.a_ptr[u];
+            const int32_t end = a.a_ptr[u + 1];
+            int32_t hi = end;
+            while (lo < hi) {
+              const int32_t mid = (lo + hi) >> 1;
+              if (__ldg(a.a_idx + mid) < hv) lo = mid + 1; else hi = mid;
+            }
+            if (lo < end && __ldg(a.a_idx + lo) == hv) adj |= 1ull << j;
+          }
+        }
+      }
+      // In id order with a narrow chunk (the first round) the earlier
+      // vertices have ids in [id_lo, w), so in the id-sorted vtxs(v) they sit
+      // right before w's own entry (its CSC index tp): read backwards from
+      // there while the ids stay >= id_lo (one window of 32 per step, usually
+      // one step); the mirror words of those entries carry the queue
+      // positions.  Four hubs per step: their first windows (ids and mirror
+      // words) are loaded together.
+      for (unsigned hm = hubs; hm && rel_hi > 0 && !wide;) {
         int32_t f[4], hb[4], id[4], x[4];
 #pragma unroll
         for (int k = 0; k < 4; k++) {
@@ -1475,13 +1515,6 @@ __global__ void __launch_bounds__(NT, 4) k_gather_w(GatherArgs a) {
             top -= 32;
           }
         }
-      }
-      for (unsigned hm = hubs; hm && rel_hi > 0 && !a.id_order; hm &= hm - 1u) {
-        const int t = __ffs(hm) - 1;
-        const int32_t hbp = __shfl_sync(kFull, bp, t), hsz = __shfl_sync(kFull, sz, t);
-        const int32_t *l = a.b_idx + hbp;
-        for (int32_t jj = lane; jj < rel_hi; jj += 32)
-          if (sorted_has(l, hsz, a.W[p0 + jj])) adj |= 1ull << jj;
       }
       __syncwarp();
     }
