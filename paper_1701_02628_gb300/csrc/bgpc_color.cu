@@ -354,8 +354,9 @@ __device__ __forceinline__ int32_t warp_kth_free_down(const uint32_t *g, int32_t
 
 // One warp: the first-fit summary of a large vertex from its forbidden
 // bitmap bm (`words` words, read only) into rec[kSumInts]; the owner of a net
-// larger than T (so > T) with a k-th free color also leaves the bitmap words
-// up to color so - 1 in lb, for the resolve's tests of overlay colors.
+// larger than T (so > T) with a k-th free color and an earlier neighbour in
+// its chunk also leaves the bitmap words up to color so - 1 in lb, for the
+// resolve's tests of overlay colors.
 // The summary's reverse first-fit part, count and mask (its first-fit list
 // already in rec[0, kSumCand)).
 __device__ __forceinline__ void warp_summarize_rest(const uint32_t *bm, int32_t so, int32_t T,
@@ -368,8 +369,10 @@ __device__ __forceinline__ void warp_summarize_rest(const uint32_t *bm, int32_t 
     rec[2 * kSumCand] = rc;
     *reinterpret_cast<unsigned long long *>(rec + 2 * kSumCand + 2) = adj;
   }
-  if (rc > 0) {
+  if (rc > 0 && adj != 0ull) {
     // the resolve tests overlay colors in (ak, so - 1] only, ak = the k-th
+    // (and only for a vertex with an earlier neighbour in its chunk: the
+    // others are colored from the summary alone)
     const int32_t ak = rec[kSumCand];
     const uint4 *b4 = reinterpret_cast<const uint4 *>(bm);
     uint4 *l4 = reinterpret_cast<uint4 *>(lb);
