@@ -464,7 +464,7 @@ int color_impl(bgpc_ctx_t *ctx, const bgpc_graph_t &g, const bgpc_opts_t &o, int
                                 (uint32_t)(cap - 1), ctx->lose.p, &ctx->dev->err, sms, s);
     } else {
       nk += launch_detect(g.b_ptr, n_b, ctx->nc.p, ctx->npos.p, ctx->bigd.p, nbig_d,
-                          ctx->dtab.p, cbw, nslots, ctx->lose.p, sms, s);
+                          ctx->dtab.p, cbw, nslots, o.rank ? 0 : 1, ctx->lose.p, sms, s);
     }
     nk += launch_compact(ctx->lose.p, W, m, ctx->newpos.p, Wn, ctx->blocksum.p, g.a_ptr,
                          ctx->dev, s);

@@ -106,10 +106,12 @@ __global__ void k_trav(const int32_t *__restrict__ a_ptr, const int32_t *__restr
 // Warp tier: one warp per net with at most 32 members.  Members outside W
 // never share a color with a W member (their colors were forbidden), so
 // only W members take part; a member loses when a member of its color
-// class has a smaller position.
+// class has a smaller position.  In id order (W sorted by id, and a net's
+// members too) the W positions grow along the member list, so that member
+// is simply an earlier lane of the class.
 __global__ void k_detect_warp(const int32_t *__restrict__ b_ptr, int32_t n_b,
                               const int32_t *__restrict__ nc, const int32_t *__restrict__ npos,
-                              uint8_t *__restrict__ lose) {
+                              int32_t id_order, uint8_t *__restrict__ lose) {
   const int lane = threadIdx.x & 31;
   int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -122,6 +124,10 @@ __global__ void k_detect_warp(const int32_t *__restrict__ b_ptr, int32_t n_b,
       if (pos >= 0) col = nc[beg + lane];
     }
     const unsigned grp = __match_any_sync(kFull, col);
+    if (id_order) {
+      if (pos >= 0 && (grp & ((1u << lane) - 1u))) lose[pos] = 1;
+      continue;
+    }
     int32_t minpos = (pos >= 0) ? pos : INT32_MAX;
 #pragma unroll
     for (int k = 0; k < 32; k++) {
@@ -139,12 +145,14 @@ __global__ void __launch_bounds__(kNT) k_detect_table(const int32_t *__restrict_
                                                       const int32_t *__restrict__ nc,
                                                       const int32_t *__restrict__ npos,
                                                       const int32_t *__restrict__ bigd,
-                                                      int32_t nbig, int32_t *__restrict__ dtab,
+                                                      int32_t nbig, int32_t min_size,
+                                                      int32_t *__restrict__ dtab,
                                                       int32_t tabcap, uint8_t *__restrict__ lose) {
   int32_t *tab = dtab + (size_t)blockIdx.x * (size_t)tabcap;
   for (int32_t b = blockIdx.x; b < nbig; b += gridDim.x) {
     const int32_t v = bigd[b];
     const int32_t beg = b_ptr[v], end = b_ptr[v + 1];
+    if (end - beg <= min_size) continue;  // taken by the mid tier
     for (int32_t f = beg + threadIdx.x; f < end; f += kNT) {
       const int32_t pos = npos[f];
       if (pos >= 0) {
@@ -169,6 +177,70 @@ __global__ void __launch_bounds__(kNT) k_detect_table(const int32_t *__restrict_
       }
     }
     __syncthreads();
+  }
+}
+
+// Mid tier, id order: one warp per net of 33 to kMidMax members.  The W
+// positions grow along the member list, so a W member loses when an earlier
+// member of the net has its color: chunks of 32 members in order, the
+// earlier lanes of a color class from __match_any_sync, the earlier chunks
+// from a per-warp set of the colors seen (open addressing in shared memory,
+// load <= 1/2, emptied after each net).
+constexpr int kMidMax = 256;
+constexpr int kMidSlots = 512;
+__global__ void __launch_bounds__(kNT) k_detect_mid(const int32_t *__restrict__ b_ptr,
+                                                    const int32_t *__restrict__ nc,
+                                                    const int32_t *__restrict__ npos,
+                                                    const int32_t *__restrict__ bigd, int32_t nbig,
+                                                    uint8_t *__restrict__ lose) {
+  constexpr int NW = kNT / 32;
+  __shared__ int32_t tabs[NW][kMidSlots];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int32_t *tab = tabs[warp];
+  for (int x = lane; x < kMidSlots; x += 32) tab[x] = -1;
+  __syncwarp();
+  const unsigned below = (1u << lane) - 1u;
+  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t b = gw; b < nbig; b += nw) {
+    const int32_t v = bigd[b];
+    const int32_t beg = b_ptr[v], size = b_ptr[v + 1] - beg;
+    if (size > kMidMax) continue;
+    int32_t used[kMidMax / 32];  // the slot this lane filled in each chunk, or -1
+#pragma unroll
+    for (int c = 0; c < kMidMax / 32; c++) {
+      used[c] = -1;
+      const int32_t k = c * 32 + lane;
+      if (c * 32 >= size) continue;  // warp-uniform
+      int32_t pos = -1, col = -1 - lane;  // distinct dummies outside W and past the end
+      if (k < size) {
+        pos = npos[beg + k];
+        if (pos >= 0) col = nc[beg + k];
+      }
+      const unsigned grp = __match_any_sync(kFull, col);
+      const bool first = (grp & below) == 0u;  // the class's first lane in this chunk
+      bool seen = false;
+      if (pos >= 0 && first) {
+        uint32_t h = ((uint32_t)col * 0x9E3779B1u) >> 23;  // 9 bits: kMidSlots
+        for (;;) {
+          const int32_t t = tab[h];
+          if (t == col) { seen = true; break; }
+          if (t == -1) {
+            const int32_t o = atomicCAS(&tab[h], -1, col);
+            if (o == -1) { used[c] = (int32_t)h; break; }
+            if (o == col) { seen = true; break; }
+          }
+          h = (h + 1) & (kMidSlots - 1);
+        }
+      }
+      const bool seen_g = __shfl_sync(kFull, seen, __ffs(grp) - 1);
+      if (pos >= 0 && (!first || seen_g)) lose[pos] = 1;
+    }
+    __syncwarp();
+#pragma unroll
+    for (int c = 0; c < kMidMax / 32; c++)
+      if (used[c] >= 0) tab[used[c]] = -1;
+    __syncwarp();
   }
 }
 
@@ -434,15 +506,20 @@ int launch_trav(const int32_t *a_ptr, const int32_t *W, const int32_t *d2tot, in
 
 int launch_detect(const int32_t *b_ptr, int32_t n_b, const int32_t *nc, const int32_t *npos,
                    const int32_t *bigd, int32_t nbigd, int32_t *dtab, int32_t tabcap,
-                   int32_t nslots, uint8_t *lose, int sms, cudaStream_t s) {
+                   int32_t nslots, int32_t id_order, uint8_t *lose, int sms, cudaStream_t s) {
   int n = 0;
   if (n_b > 0) {
-    k_detect_warp<<<warps_grid(n_b, sms), kNT, 0, s>>>(b_ptr, n_b, nc, npos, lose);
+    k_detect_warp<<<warps_grid(n_b, sms), kNT, 0, s>>>(b_ptr, n_b, nc, npos, id_order, lose);
+    n++;
+  }
+  if (nbigd > 0 && id_order) {
+    k_detect_mid<<<warps_grid(nbigd, sms), kNT, 0, s>>>(b_ptr, nc, npos, bigd, nbigd, lose);
     n++;
   }
   if (nbigd > 0) {
     int grid = nbigd < nslots ? nbigd : nslots;
-    k_detect_table<<<grid, kNT, 0, s>>>(b_ptr, nc, npos, bigd, nbigd, dtab, tabcap, lose);
+    k_detect_table<<<grid, kNT, 0, s>>>(b_ptr, nc, npos, bigd, nbigd, id_order ? kMidMax : 0,
+                                        dtab, tabcap, lose);
     n++;
   }
   return n;

@@ -369,7 +369,7 @@ int launch_trav(const int32_t *a_ptr, const int32_t *W, const int32_t *d2tot, in
                 int32_t small_ok, DevScalars *dev, cudaStream_t s);
 int launch_detect(const int32_t *b_ptr, int32_t n_b, const int32_t *nc, const int32_t *npos,
                    const int32_t *bigd, int32_t nbigd, int32_t *dtab, int32_t tabcap,
-                   int32_t nslots, uint8_t *lose, int sms, cudaStream_t s);
+                   int32_t nslots, int32_t id_order, uint8_t *lose, int sms, cudaStream_t s);
 int launch_detect_pairs(const int32_t *a_ptr, const int32_t *a_idx, const int32_t *W, int32_t m,
                         const int32_t *colors, unsigned long long *keys, uint32_t *vals,
                         uint32_t mask, uint8_t *lose, int32_t *err, int sms, cudaStream_t s);
