@@ -222,7 +222,9 @@ int color_impl(bgpc_ctx_t *ctx, const bgpc_graph_t &g, const bgpc_opts_t &o, int
     nk += launch_tpos(g, ctx->tpos.p, scratch, ctx->thist.p, ctx->tsums.p, o.validate,
                       &ctx->dev->err, ctx->hub_id.p, n_b > 0 ? ctx->ihub.p : nullptr, sms, s);
   }
-  nk += launch_vertex_static(g, ctx->tpos.p, ctx->s_own.p, ctx->d2tot.p, ctx->nown.p,
+  // the owner flags serve the reverse offsets' net scan, used for caller ranks only
+  nk += launch_vertex_static(g, ctx->tpos.p, ctx->s_own.p, ctx->d2tot.p,
+                             o.rank ? ctx->nown.p : nullptr,
                              o.net_rounds > 0 ? ctx->netc.p : nullptr, center_first,
                              ctx->ownid.p, sms, s);
   nk += launch_init_queue(o.rank, n_a, ctx->W0.p, &ctx->dev->err, s);

@@ -1982,9 +1982,18 @@ __global__ void __launch_bounds__(256) k_hub_build(const int32_t *__restrict__ b
     for (int32_t x = threadIdx.x; x < words; x += blockDim.x) s_bm[x] = 0u;
     __syncthreads();
     const int32_t v = hub_net[h];
-    for (int32_t f = b_ptr[v] + threadIdx.x; f < b_ptr[v + 1]; f += blockDim.x) {
-      const int32_t c = nc[f];
-      if (c >= 0 && c < lim) atomicOr(&s_bm[c >> 5], 1u << (c & 31));
+    const int32_t beg = b_ptr[v], end = b_ptr[v + 1];
+    // four members per thread and step, their loads issued together
+    for (int32_t f0 = beg + threadIdx.x; f0 < end; f0 += 4 * blockDim.x) {
+      int32_t c[4];
+#pragma unroll
+      for (int q = 0; q < 4; q++) {
+        const int32_t f = f0 + q * (int32_t)blockDim.x;
+        c[q] = f < end ? nc[f] : -1;
+      }
+#pragma unroll
+      for (int q = 0; q < 4; q++)
+        if (c[q] >= 0 && c[q] < lim) atomicOr(&s_bm[c[q] >> 5], 1u << (c[q] & 31));
     }
     __syncthreads();
     for (int32_t x = threadIdx.x; x < words; x += blockDim.x)
@@ -2007,7 +2016,7 @@ int launch_hub_build(const int32_t *b_ptr, const int32_t *nc, const int32_t *hub
                      int32_t nhub, int32_t words, uint32_t *nbm, int sms, cudaStream_t s) {
   if (nhub <= 0) return 0;
   if (allow_dynamic_smem(k_hub_build) != cudaSuccess) return 0;  // reported by the caller
-  const int grid = nhub < sms * 4 ? nhub : sms * 4;
+  const int grid = nhub < sms * 8 ? nhub : sms * 8;  // one resident set at 256 threads
   k_hub_build<<<grid, 256, (size_t)words * 4, s>>>(b_ptr, nc, hub_net, nhub, words, nbm);
   return 1;
 }

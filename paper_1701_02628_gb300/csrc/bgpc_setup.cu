@@ -232,10 +232,13 @@ __global__ void k_vertex_static(const int32_t *__restrict__ a_ptr,
       d2tot[w] = (int32_t)sum;
       if (netc && end == beg) netc[w] = -1;
     }
-    for (int32_t i = beg + lane; i < end; i += 32) {
+    // the owner flags per CSC entry (nown may be NULL: not needed in id
+    // order) and the N1 proposal from the owner entry's CSC position
+    for (int32_t i = beg + lane; i < end && (nown || netc); i += 32) {
       const bool mine = a_idx[i] == own;
+      if (!nown && !mine) continue;
       const int32_t f = tpos[i];
-      nown[f] = mine ? 1 : 0;
+      if (nown) nown[f] = mine ? 1 : 0;
       if (netc && mine) {
         int32_t k = f - b_ptr[own];
         if (center_first) k = ((int32_t)w == own) ? 0 : k + 1 - (own < (int32_t)w ? 1 : 0);
