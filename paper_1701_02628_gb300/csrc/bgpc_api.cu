@@ -460,9 +460,8 @@ int color_impl(bgpc_ctx_t *ctx, const bgpc_graph_t &g, const bgpc_opts_t &o, int
                        o.detect != BGPC_DETECT_NETS &&
                        (o.detect == BGPC_DETECT_PAIRS || incid_w * 4 <= (int64_t)nnz);
     if (pairs) {
-      CU(grow(ctx->pkeys, (size_t)cap));
-      CU(grow(ctx->pvals, (size_t)cap));
-      nk += launch_detect_pairs(g.a_ptr, g.a_idx, W, m, colors, ctx->pkeys.p, ctx->pvals.p,
+      CU(grow(ctx->pkeys, 2 * (size_t)cap));
+      nk += launch_detect_pairs(g.a_ptr, g.a_idx, W, m, colors, ctx->pkeys.p,
                                 (uint32_t)(cap - 1), ctx->lose.p, &ctx->dev->err, sms, s);
     } else {
       nk += launch_detect(g.b_ptr, n_b, ctx->nc.p, ctx->npos.p, ctx->bigd.p, nbig_d,
@@ -914,7 +913,6 @@ int bgpc_ctx_destroy(bgpc_ctx_t *ctx) {
   release(ctx->cptr); release(ctx->cidx); release(ctx->dtab); release(ctx->vtab);
   release(ctx->wlist); release(ctx->segoff); release(ctx->segmap); release(ctx->gbm);
   release(ctx->gcnt); release(ctx->gsum); release(ctx->lbm); release(ctx->pkeys);
-  release(ctx->pvals);
   release(ctx->gadj);
   if (ctx->h_wlist) cudaFreeHost(ctx->h_wlist);
   for (bgpc_ctx_t *sub : ctx->subs) bgpc_ctx_destroy(sub);

@@ -270,8 +270,8 @@ __device__ __forceinline__ uint32_t pair_hash(unsigned long long k) {
 
 __global__ void k_pairs_insert(const int32_t *__restrict__ a_ptr, const int32_t *__restrict__ a_idx,
                                const int32_t *__restrict__ W, int32_t m,
-                               const int32_t *__restrict__ colors, unsigned long long *keys,
-                               uint32_t *vals, uint32_t mask, int32_t *err) {
+                               const int32_t *__restrict__ colors, unsigned long long *kv,
+                               uint32_t mask, int32_t *err) {
   const int lane = threadIdx.x & 31;
   int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -287,10 +287,10 @@ __global__ void k_pairs_insert(const int32_t *__restrict__ a_ptr, const int32_t 
           atomicOr(err, ERR_INTERNAL);
           break;
         }
-        unsigned long long k = __ldcg(keys + slot);
-        if (k == kEmptyKey) k = atomicCAS(keys + slot, kEmptyKey, key);
+        unsigned long long k = __ldcg(kv + 2 * (size_t)slot);
+        if (k == kEmptyKey) k = atomicCAS(kv + 2 * (size_t)slot, kEmptyKey, key);
         if (k == kEmptyKey || k == key) {
-          atomicMin(vals + slot, (uint32_t)p);
+          atomicMin(reinterpret_cast<uint32_t *>(kv + 2 * (size_t)slot + 1), (uint32_t)p);
           break;
         }
         slot = (slot + 1) & mask;
@@ -302,8 +302,7 @@ __global__ void k_pairs_insert(const int32_t *__restrict__ a_ptr, const int32_t 
 __global__ void k_pairs_lookup(const int32_t *__restrict__ a_ptr, const int32_t *__restrict__ a_idx,
                                const int32_t *__restrict__ W, int32_t m,
                                const int32_t *__restrict__ colors,
-                               const unsigned long long *__restrict__ keys,
-                               const uint32_t *__restrict__ vals, uint32_t mask,
+                               const unsigned long long *__restrict__ kv, uint32_t mask,
                                uint8_t *__restrict__ lose, int32_t *err) {
   const int lane = threadIdx.x & 31;
   int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -317,9 +316,9 @@ __global__ void k_pairs_lookup(const int32_t *__restrict__ a_ptr, const int32_t 
       const unsigned long long key = pair_key(a_idx[i], c);
       uint32_t slot = pair_hash(key) & mask;
       for (uint32_t probe = 0;; probe++) {
-        const unsigned long long k = keys[slot];
+        const unsigned long long k = kv[2 * (size_t)slot];
         if (k == key) {
-          l = vals[slot] < (uint32_t)p;
+          l = reinterpret_cast<const uint32_t *>(kv + 2 * (size_t)slot + 1)[0] < (uint32_t)p;
           break;
         }
         if (k == kEmptyKey || probe > mask) {  // every pair inserted its key
@@ -526,15 +525,16 @@ int launch_detect(const int32_t *b_ptr, int32_t n_b, const int32_t *nc, const in
 }
 
 int launch_detect_pairs(const int32_t *a_ptr, const int32_t *a_idx, const int32_t *W, int32_t m,
-                        const int32_t *colors, unsigned long long *keys, uint32_t *vals,
-                        uint32_t mask, uint8_t *lose, int32_t *err, int sms, cudaStream_t s) {
+                        const int32_t *colors, unsigned long long *kv, uint32_t mask,
+                        uint8_t *lose, int32_t *err, int sms, cudaStream_t s) {
   if (m <= 0) return 0;
   const size_t cap = (size_t)mask + 1;
-  cudaMemsetAsync(keys, 0xff, sizeof(unsigned long long) * cap, s);
-  cudaMemsetAsync(vals, 0xff, sizeof(uint32_t) * cap, s);
+  // slot i: the key at kv[2i], the smallest position in the low word of
+  // kv[2i + 1] (both in one 32-byte sector); all ones = empty / no position
+  cudaMemsetAsync(kv, 0xff, 2 * sizeof(unsigned long long) * cap, s);
   const int grid = warps_grid(m, sms);
-  k_pairs_insert<<<grid, kNT, 0, s>>>(a_ptr, a_idx, W, m, colors, keys, vals, mask, err);
-  k_pairs_lookup<<<grid, kNT, 0, s>>>(a_ptr, a_idx, W, m, colors, keys, vals, mask, lose, err);
+  k_pairs_insert<<<grid, kNT, 0, s>>>(a_ptr, a_idx, W, m, colors, kv, mask, err);
+  k_pairs_lookup<<<grid, kNT, 0, s>>>(a_ptr, a_idx, W, m, colors, kv, mask, lose, err);
   return 2;
 }
 

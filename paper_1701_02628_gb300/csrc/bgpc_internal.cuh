@@ -178,8 +178,8 @@ struct bgpc_ctx {
   size_t h_wlist_cap = 0;
   bgpc::Buf<int32_t> cptr, cidx;       // D2GC closed neighbourhoods
   bgpc::Buf<int32_t> dtab;             // per-slot color tables (detection)
-  bgpc::Buf<unsigned long long> pkeys; // pair-tier detection: (net, color) keys
-  bgpc::Buf<uint32_t> pvals;           // ... and the smallest position per key
+  bgpc::Buf<unsigned long long> pkeys; // pair-tier detection: slots of (net, color) key and
+                                       // smallest position, 16 bytes each
   bgpc::Buf<int32_t> vtab;             // per-slot color counts (validation)
   size_t dtab_filled = 0;              // entries of dtab already set to INT_MAX
   bgpc::Buf<unsigned long long> card;  // color-set cardinalities
@@ -371,8 +371,8 @@ int launch_detect(const int32_t *b_ptr, int32_t n_b, const int32_t *nc, const in
                    const int32_t *bigd, int32_t nbigd, int32_t *dtab, int32_t tabcap,
                    int32_t nslots, int32_t id_order, uint8_t *lose, int sms, cudaStream_t s);
 int launch_detect_pairs(const int32_t *a_ptr, const int32_t *a_idx, const int32_t *W, int32_t m,
-                        const int32_t *colors, unsigned long long *keys, uint32_t *vals,
-                        uint32_t mask, uint8_t *lose, int32_t *err, int sms, cudaStream_t s);
+                        const int32_t *colors, unsigned long long *kv, uint32_t mask,
+                        uint8_t *lose, int32_t *err, int sms, cudaStream_t s);
 int launch_compact(const uint8_t *lose, const int32_t *W, int32_t m, int32_t *newpos,
                     int32_t *Wn, int32_t *blocksum, const int32_t *a_ptr, DevScalars *dev,
                     cudaStream_t s);
