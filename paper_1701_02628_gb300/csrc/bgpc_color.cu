@@ -884,17 +884,35 @@ __global__ void __launch_bounds__(NT) k_color_wave(WaveArgs a) {
     // ---- step S (first fit): the large vertices' summaries from the gather
     const unsigned long long large = s_large;
     if constexpr (POLICY == BGPC_FF) {
-      for (int32_t iv = warp; iv < n; iv += NW) {
-        if (!((large >> iv) & 1ull)) continue;
-        const int32_t *rec = a.gsum + (slot0 + iv) * kSumInts;
-        const int32_t f0 = rec[lane], f1 = rec[32 + lane];
-        const int32_t r0 = rec[kSumCand + lane], r1 = rec[kSumCand + 32 + lane];
-        const int32_t rc = (s_sown[iv] > a.T) ? rec[2 * kSumCand] : 0;
-        s_list[iv][lane] = rc > 0 ? -r0 : f0;
-        s_list[iv][lane + 32] = rc > 0 ? -r1 : f1;
-        if (lane == 0) {
-          s_rcnt[iv] = rc;
-          s_adj[iv] = *reinterpret_cast<const unsigned long long *>(rec + 2 * kSumCand + 2);
+      // two vertices per warp and step, their loads issued together
+      for (int32_t iv0 = warp; iv0 < n; iv0 += 2 * NW) {
+        int32_t f0[2], f1[2], r0[2], r1[2], rc[2];
+        unsigned long long am[2];
+        bool lg[2];
+#pragma unroll
+        for (int h = 0; h < 2; h++) {
+          const int32_t iv = iv0 + h * NW;
+          lg[h] = iv < n && ((large >> iv) & 1ull);
+          const int32_t *rec = a.gsum + (slot0 + (lg[h] ? iv : 0)) * kSumInts;
+          f0[h] = lg[h] ? rec[lane] : 0;
+          f1[h] = lg[h] ? rec[32 + lane] : 0;
+          r0[h] = lg[h] ? rec[kSumCand + lane] : 0;
+          r1[h] = lg[h] ? rec[kSumCand + 32 + lane] : 0;
+          rc[h] = (lg[h] && s_sown[iv] > a.T) ? rec[2 * kSumCand] : 0;
+          am[h] = (lg[h] && lane == 0)
+                      ? *reinterpret_cast<const unsigned long long *>(rec + 2 * kSumCand + 2)
+                      : 0ull;
+        }
+#pragma unroll
+        for (int h = 0; h < 2; h++) {
+          if (!lg[h]) continue;
+          const int32_t iv = iv0 + h * NW;
+          s_list[iv][lane] = rc[h] > 0 ? -r0[h] : f0[h];
+          s_list[iv][lane + 32] = rc[h] > 0 ? -r1[h] : f1[h];
+          if (lane == 0) {
+            s_rcnt[iv] = rc[h];
+            s_adj[iv] = am[h];
+          }
         }
       }
       __syncthreads();
