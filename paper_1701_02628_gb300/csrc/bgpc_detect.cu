@@ -41,7 +41,9 @@ __device__ __forceinline__ int32_t block_excl_scan(int32_t v, int32_t *red, int3
 }
 
 // k for each owner of a net with |vtxs| > T that is in W: the number of
-// members before it in vtxs order that are in W and own the same net.
+// members before it in vtxs order that are in W and own the same net.  Used
+// when W follows a caller's rank; in id order the same k comes from a sort
+// of the W positions by owner net (launch_kofs_sorted), in work |W|.
 __global__ void __launch_bounds__(kNT) k_kofs(const int32_t *__restrict__ b_ptr,
                                               const int32_t *__restrict__ npos,
                                               const uint8_t *__restrict__ nown,
