@@ -613,8 +613,9 @@ def run_gpu(args):
     dom_ms, dom_bytes, dom_entries = kern[dom]
     peak, peak_kind = peaks()
     achieved = dom_bytes / (dom_ms / 1000.0) / 1e9 if dom_ms > 0 else 0.0
-    # the survey's model: 8 B (an index and a gathered color) per traversed
-    # two-hop entry, hub entries included although they are read as bitmaps
+    # the vertex-based formulation's model: 8 B (an index and a gathered
+    # color) per traversed two-hop entry, hub entries included although they
+    # are read as bitmaps
     eff8 = 8 * dom_entries / (dom_ms / 1000.0) / 1e9 if dom_ms > 0 else 0.0
     phase_ms = {k: tot(k) / args.steps
                 for k in ("ms_setup", "ms_gather", "ms_color", "ms_publish", "ms_detect")}
