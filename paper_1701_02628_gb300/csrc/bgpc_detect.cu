@@ -415,10 +415,17 @@ __global__ void k_relabel(const int32_t *__restrict__ a_ptr, const int32_t *__re
     const bool l = lose[p] != 0;
     const int32_t np = l ? newpos[p] : -1;
     const int32_t beg = a_ptr[w], end = a_ptr[w + 1];
-    for (int32_t i = beg + lane; i < end; i += 32) {
-      const int32_t f = tpos[i];
-      npos[f] = np;
-      if (l) nc[f] = -2 - np;
+    // four CSR->CSC entries per lane and step, their loads issued together
+    for (int32_t i0 = beg + lane; i0 < end; i0 += 128) {
+      int32_t f[4];
+#pragma unroll
+      for (int q = 0; q < 4; q++) f[q] = i0 + 32 * q < end ? tpos[i0 + 32 * q] : -1;
+#pragma unroll
+      for (int q = 0; q < 4; q++) {
+        if (f[q] < 0) continue;
+        npos[f[q]] = np;
+        if (l) nc[f[q]] = -2 - np;
+      }
     }
     __syncwarp();
     if (lane == 0) {
